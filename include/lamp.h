@@ -1,0 +1,210 @@
+/*
+ * lamp.h — C ABI of the GB300 (sm_103a) implementation of Log-Averaged Mirror
+ * Prox (LAMP, arXiv 2511.11359) for discrete optimal transport
+ *
+ *     min_{X in Pi(r,c)} <C, X>                      (Eq. prob:primal_ot)
+ *
+ * through the l1-penalised saddle problem (Eq. prob:spp), solved by Alg. 2:
+ * a dual-only mirror-prox iteration whose primal coupling
+ *
+ *     X = diag(r) p^{eta_t}(nu),   p^{eta}(nu)_ij = exp(-(C_ij + 2K nu_j)/eta) / Z_i
+ *
+ * (Eq. def:dual_to_primal, K = ||C||_inf) is never stored: every iteration
+ * makes one fused pass that computes the row log-normalisers log Z_i and the
+ * column marginals col(X) of the two couplings the iteration needs
+ * (Section 4.1), in O(n + m) memory.
+ *
+ * Conventions for every entry point
+ *   - Return value: LAMP_OK (0) or one of the LAMP_E_* codes below.  On error
+ *     lamp_last_error(ctx) returns a one-line description (ctx may be NULL for
+ *     errors raised before a context exists; the message is then thread-local).
+ *   - Device pointers are CUDA global-memory pointers of the device that is
+ *     current when lamp_create is called.  Host pointers are ordinary memory.
+ *   - Input buffers are borrowed: the caller keeps them alive and unchanged
+ *     for the lifetime of the context.  The library never copies or stores C
+ *     and never forms X.
+ *   - All device work goes to the CUDA stream given to lamp_create (NULL = the
+ *     legacy default stream).  Entry points that return results to host memory
+ *     synchronise that stream before returning.
+ *   - Floating point: costs and points are float32; marginals, potentials and
+ *     all reported scalars are float64.  The inner loops run in float32 with a
+ *     compensated exponent; row/column sums are combined in float64.
+ *   - Not thread-safe per context; distinct contexts may be used concurrently.
+ */
+#ifndef LAMP_H_
+#define LAMP_H_
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LAMP_API __attribute__((visibility("default")))
+#else
+#define LAMP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LAMP_OK 0
+#define LAMP_E_INVALID 1        /* bad argument: sizes, pointers, parameters, marginals */
+#define LAMP_E_CUDA 2           /* a CUDA runtime call failed (message holds its text)  */
+#define LAMP_E_NOMEM 3          /* device allocation failed                             */
+#define LAMP_E_NOT_CONVERGED 4  /* lamp_solve hit max_iter; the result is still valid    */
+#define LAMP_E_NUMERIC 5        /* a non-finite or out-of-range sum appeared            */
+#define LAMP_E_TIMEOUT 6        /* a device-side wait ran out of its iteration budget   */
+#define LAMP_E_UNSUPPORTED 7    /* valid request this build does not implement          */
+
+typedef struct lamp_ctx lamp_ctx;
+
+/* How the cost matrix is given. */
+typedef enum {
+  LAMP_COST_DENSE = 0,    /* stored n x m float32 matrix C, row-major with leading dimension ldc */
+  LAMP_COST_SQEUCLID = 1  /* C_ij = cost_scale * |x_i - y_j|^2 generated on the fly from points */
+} lamp_cost_kind;
+
+/* Arithmetic of the cost generation for LAMP_COST_SQEUCLID. */
+typedef enum {
+  LAMP_PREC_FP32 = 0,     /* x.y in float32 on CUDA cores                                  */
+  LAMP_PREC_BF16_TC = 1   /* x.y with bf16-rounded points on tcgen05 tensor cores, float32
+                             accumulation; the problem solved is the one of the rounded points */
+} lamp_precision;
+
+/*
+ * Problem data (Section 2.1).  All pointers are DEVICE pointers and borrowed.
+ *   n, m      number of source / target supports, n >= 1, m >= 1, n*m < 2^62.
+ *   d         point dimension for LAMP_COST_SQEUCLID (1 <= d <= 64); ignored for DENSE.
+ *   kind      lamp_cost_kind.
+ *   C, ldc    DENSE: row-major n x m float32, entry (i,j) at C[i*ldc + j], ldc >= m,
+ *             entries >= 0 and finite (C in R_+^{n x m}, Alg. 2).
+ *   x, y      SQEUCLID: row-major n x d and m x d float32 point coordinates.
+ *   r, c      float64 marginals, entries > 0, each summing to 1 within 1e-9
+ *             (r in Delta^n, c in Delta^m with full support, Lemma l1_prob_equiv).
+ *   cost_scale  SQEUCLID multiplier s of |x - y|^2: s > 0 uses s as given; s = 0
+ *             means 1; s < 0 means 1 / max_ij |x_i - y_j|^2 (cost normalised to max 1).
+ */
+typedef struct {
+  int64_t n, m, d;
+  int32_t kind;
+  int32_t _pad0;
+  const float* C;
+  int64_t ldc;
+  const float* x;
+  const float* y;
+  const double* r;
+  const double* c;
+  double cost_scale;
+} lamp_problem;
+
+/*
+ * Alg. 2 parameters.  lamp_params_default fills the paper's experimental
+ * settings (App. E.2): eta = 0, tau1 = tau2 = 1/(2K), alpha = 0.01, beta = 1.1.
+ *   eta        entropic coefficient >= 0, in cost units (Eq. prob:primal_eot); tau1*eta <= 1.
+ *   tau1, tau2 primal / dual step sizes; 0 means 1/(2K).
+ *   alpha      dual-entropy smoothing, c^alpha = c + alpha/m (Section 3.1), > 0.
+ *   beta       clip level of tclip (Section 3.1), > 0.
+ *   tol        L1 infeasibility target of lamp_solve: stop at the first t with
+ *              ||col(X^t) - c||_1 + ||row(X^t) - r||_1 <= tol (App. E.2).
+ *   max_iter   lamp_solve stops at iteration index t = max_iter at the latest.
+ *   check_every how many iterations run on the device between host polls (>= 1).
+ *   prec       lamp_precision (SQEUCLID only).
+ *   K          0: ||C||_inf computed on the device from the cost the kernels use;
+ *              > 0: use this value for K.
+ */
+typedef struct {
+  double eta, tau1, tau2, alpha, beta, tol;
+  int64_t max_iter, check_every;
+  int32_t prec;
+  int32_t _pad0;
+  double K;
+} lamp_params;
+
+/* Summary of the current state (all host values).
+ *   iters    iteration index t of the state (number of updates applied).
+ *   infeas   ||col(X^t) - c||_1 + ||row(X^t) - r||_1 (float64 sums).
+ *   obj_CX   <C, X^t>.
+ *   kappa    1/eta_t.   K  the ||C||_inf in use.   status  LAMP_OK, LAMP_E_NOT_CONVERGED or LAMP_E_NUMERIC. */
+typedef struct {
+  int64_t iters;
+  double infeas, obj_CX, kappa, K;
+  int32_t status;
+  int32_t _pad0;
+} lamp_result;
+
+/* Fill *p with the defaults listed above (tol = 1e-6, max_iter = 100000, check_every = 50). */
+LAMP_API int lamp_params_default(lamp_params* p);
+
+/* Validate the problem and parameters, allocate the O(n + m) device workspace,
+ * compute K (unless given) and the cost scale, and set the Alg. 2 start
+ * (theta = nu = 0, eta_0 = infinity).  stream: a cudaStream_t, or NULL.
+ * Errors: LAMP_E_INVALID (nothing allocated), LAMP_E_NOMEM, LAMP_E_CUDA. */
+LAMP_API int lamp_create(lamp_ctx** out, const lamp_problem* prob, const lamp_params* params, void* stream);
+
+/* Run Alg. 2 from the current state until the infeasibility of X^t is <= tol
+ * or t reaches max_iter (App. E.2 termination, checked on X^t before the
+ * iteration's updates).  The state left in the context is that X^t's state.
+ * Returns LAMP_OK, LAMP_E_NOT_CONVERGED (max_iter reached; *out is valid),
+ * LAMP_E_NUMERIC or LAMP_E_CUDA.  out may be NULL. */
+LAMP_API int lamp_solve(lamp_ctx* ctx, lamp_result* out);
+
+/* Apply exactly `iters` iterations of Alg. 2 to the current state with no
+ * termination test (iters >= 0).  Asynchronous on the context's stream. */
+LAMP_API int lamp_iterate(lamp_ctx* ctx, int64_t iters);
+
+/* Evaluate the current state t: one fused pass computing col(X^t), log Z and
+ * the objective quantities, written to host memory (synchronises):
+ *   out[0] <C, X^t>             out[1] ||col(X^t) - c||_1   out[2] ||row(X^t) - r||_1
+ *   out[3] H(X^t)               (entropy identity of App. D, from O(n+m) values)
+ *   out[4] P^eta(X^t)           (Eq. prob:l1_ot_primal)
+ *   out[5] certificate RHS 4K||col-c||_1 + 2K log m / t (Prop. infeas_bound (a); eta = 0, t >= 1, else NaN)
+ *   out[6] saddle dual max(D(theta^t), D(nu^t)) (App. B; NaN: not computed by this build)
+ *   out[7] K */
+LAMP_API int lamp_objective(lamp_ctx* ctx, double out[8]);
+
+/* Gradient of L = <C, X> - eta H(X) at the current state's X^t with respect
+ * to the points (envelope theorem): dL/dx_i = sum_j X_ij dC_ij/dx_i and
+ * dL/dy_j = sum_i X_ij dC_ij/dy_j, with dC_ij/dx_i = 2 s (x_i - y_j).
+ * dx: device n x d float32, dy: device m x d float32 (either may be NULL).
+ * SQEUCLID only (LAMP_E_UNSUPPORTED otherwise).  Asynchronous. */
+LAMP_API int lamp_grad(lamp_ctx* ctx, float* dx, float* dy);
+
+/* Copy the state to host memory (synchronises).  nu, theta: m doubles; logZ:
+ * n doubles, the natural-log row normalisers of X^t (valid after lamp_solve or
+ * lamp_objective; NaN-filled otherwise); kappa, t: scalars; row_shifts: 2n
+ * floats, the per-row exponent shifts the next iteration will use (with them a
+ * restored run repeats the original bit for bit).  Any pointer may be NULL. */
+LAMP_API int lamp_get_state(lamp_ctx* ctx, double* nu, double* theta, double* logZ, double* kappa, int64_t* t,
+                            float* row_shifts);
+
+/* Replace the state by (nu, theta, kappa, t) from host memory (checkpoint
+ * restore): |nu_j| < 1, |theta_j| < 1, kappa >= 0, t >= 0.  row_shifts: the 2n
+ * floats from lamp_get_state, or NULL to recompute them with a row-max pass. */
+LAMP_API int lamp_set_state(lamp_ctx* ctx, const double* nu, const double* theta, double kappa, int64_t t,
+                            const float* row_shifts);
+
+/* Host-buffer variant used for end-to-end timing: copy x, y (SQEUCLID) or C
+ * (DENSE) and r, c from HOST memory into device buffers the context owns, run
+ * `iters` iterations, and copy the infeasibility of the last evaluated X^t and
+ * nu (m doubles, may be NULL) back to host memory.  The context must have been
+ * created with lamp_create_owned.  Synchronises. */
+LAMP_API int lamp_step_host(lamp_ctx* ctx, const float* C_or_x, const float* y, const double* r, const double* c,
+                   int64_t iters, double* infeas_out, double* nu_out);
+
+/* Like lamp_create, but the context allocates and owns device copies of the
+ * inputs; prob's pointers are HOST pointers and are copied once here. */
+LAMP_API int lamp_create_owned(lamp_ctx** out, const lamp_problem* host_prob, const lamp_params* params, void* stream);
+
+/* Number of kernel launches one iteration issues (for launch accounting). */
+LAMP_API int64_t lamp_launches_per_iteration(const lamp_ctx* ctx);
+
+LAMP_API const char* lamp_last_error(const lamp_ctx* ctx);
+
+/* Release everything the context owns (NULL is a no-op). */
+LAMP_API void lamp_destroy(lamp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LAMP_H_ */

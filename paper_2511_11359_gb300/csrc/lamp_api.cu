@@ -1,0 +1,668 @@
+// Host side of the LAMP C ABI (include/lamp.h): validation, the O(n + m) workspace,
+// the device loop (CUDA graphs of whole iterations, polled every check_every
+// iterations) and the O(1) bookkeeping of the objective (App. D identity,
+// Prop. infeas_bound (a)).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lamp.h"
+#include "lamp_common.cuh"
+
+using namespace lamp;
+
+struct lamp_ctx {
+  Consts k{};
+  Work w{};
+  Geometry g{};
+  Inputs in{};
+  int prec = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;  // private stream used for graph capture
+  lamp_params params{};
+  double Hr = 0.0;             // entropy of r
+  double log_m = 0.0;
+  int rowblocks = 0;
+  std::vector<void*> allocs;
+  // owned input copies (lamp_create_owned)
+  bool owned = false;
+  float* own_a = nullptr;  // C or x
+  float* own_b = nullptr;  // y
+  double* own_r = nullptr;
+  double* own_c = nullptr;
+  // graphs: [0] one iteration, [1] check_every iterations
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  int64_t glen[2] = {0, 0};
+  DevState* host_dev = nullptr;  // pinned mirror for polling
+  std::string err;
+};
+
+static thread_local std::string g_err;
+
+static int fail(lamp_ctx* ctx, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (ctx)
+    ctx->err = buf;
+  else
+    g_err = buf;
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t _e = (call);                                                              \
+    if (_e != cudaSuccess)                                                                \
+      return fail(ctx, _e == cudaErrorMemoryAllocation ? LAMP_E_NOMEM : LAMP_E_CUDA,      \
+                  "%s: %s (%s:%d)", #call, cudaGetErrorString(_e), __FILE__, __LINE__);  \
+  } while (0)
+
+template <class T>
+static int dalloc(lamp_ctx* ctx, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) return fail(ctx, LAMP_E_NOMEM, "cudaMalloc(%zu bytes): %s", count * sizeof(T),
+                                    cudaGetErrorString(e));
+  ctx->allocs.push_back(q);
+  *p = reinterpret_cast<T*>(q);
+  return LAMP_OK;
+}
+
+extern "C" int lamp_params_default(lamp_params* p) {
+  if (!p) return fail(nullptr, LAMP_E_INVALID, "lamp_params_default: null pointer");
+  std::memset(p, 0, sizeof(*p));
+  p->eta = 0.0;
+  p->tau1 = 0.0;
+  p->tau2 = 0.0;
+  p->alpha = 0.01;
+  p->beta = 1.1;
+  p->tol = 1e-6;
+  p->max_iter = 100000;
+  p->check_every = 50;
+  p->prec = LAMP_PREC_FP32;
+  p->K = 0.0;
+  return LAMP_OK;
+}
+
+// host-side validation that needs no device (so that it is testable without a GPU)
+static int validate(const lamp_problem* pr, const lamp_params* pa, bool device_ptrs) {
+  if (!pr || !pa) return fail(nullptr, LAMP_E_INVALID, "null problem or params");
+  if (pr->n < 1 || pr->m < 1) return fail(nullptr, LAMP_E_INVALID, "n and m must be >= 1 (n=%lld m=%lld)",
+                                         (long long)pr->n, (long long)pr->m);
+  if (pr->n > (int64_t(1) << 31) || pr->m > (int64_t(1) << 31))
+    return fail(nullptr, LAMP_E_INVALID, "n and m must be <= 2^31");
+  if ((double)pr->n * (double)pr->m >= 4.0e18) return fail(nullptr, LAMP_E_INVALID, "n*m too large");
+  if (pr->kind != LAMP_COST_DENSE && pr->kind != LAMP_COST_SQEUCLID)
+    return fail(nullptr, LAMP_E_INVALID, "unknown cost kind %d", pr->kind);
+  if (!pr->r || !pr->c) return fail(nullptr, LAMP_E_INVALID, "r and c must be non-null");
+  if (pr->kind == LAMP_COST_DENSE) {
+    if (!pr->C) return fail(nullptr, LAMP_E_INVALID, "DENSE cost needs C");
+    if (pr->ldc < pr->m) return fail(nullptr, LAMP_E_INVALID, "ldc (%lld) < m (%lld)", (long long)pr->ldc,
+                                     (long long)pr->m);
+  } else {
+    if (!pr->x || !pr->y) return fail(nullptr, LAMP_E_INVALID, "SQEUCLID cost needs x and y");
+    if (pr->d < 1 || pr->d > 64) return fail(nullptr, LAMP_E_INVALID, "d must be in [1, 64] (d=%lld)",
+                                             (long long)pr->d);
+    if (!std::isfinite(pr->cost_scale)) return fail(nullptr, LAMP_E_INVALID, "cost_scale must be finite");
+  }
+  if (!(pa->eta >= 0.0) || !std::isfinite(pa->eta)) return fail(nullptr, LAMP_E_INVALID, "eta must be >= 0");
+  if (!(pa->tau1 >= 0.0) || !(pa->tau2 >= 0.0) || !std::isfinite(pa->tau1) || !std::isfinite(pa->tau2))
+    return fail(nullptr, LAMP_E_INVALID, "tau1, tau2 must be >= 0 (0 = 1/(2K))");
+  if (!(pa->alpha > 0.0) || !std::isfinite(pa->alpha)) return fail(nullptr, LAMP_E_INVALID, "alpha must be > 0");
+  if (!(pa->beta > 0.0) || !std::isfinite(pa->beta)) return fail(nullptr, LAMP_E_INVALID, "beta must be > 0");
+  if (std::isnan(pa->tol)) return fail(nullptr, LAMP_E_INVALID, "tol is NaN");
+  if (pa->max_iter < 0) return fail(nullptr, LAMP_E_INVALID, "max_iter must be >= 0");
+  if (pa->check_every < 1 || pa->check_every > 100000)
+    return fail(nullptr, LAMP_E_INVALID, "check_every must be in [1, 100000]");
+  if (pa->prec != LAMP_PREC_FP32 && pa->prec != LAMP_PREC_BF16_TC)
+    return fail(nullptr, LAMP_E_INVALID, "unknown precision %d", pa->prec);
+  if (pa->prec == LAMP_PREC_BF16_TC)
+    return fail(nullptr, LAMP_E_UNSUPPORTED, "LAMP_PREC_BF16_TC is not available in this build");
+  if (!(pa->K >= 0.0) || !std::isfinite(pa->K)) return fail(nullptr, LAMP_E_INVALID, "K must be >= 0");
+  if (pa->tau1 > 0.0 && pa->tau1 * pa->eta > 1.0) return fail(nullptr, LAMP_E_INVALID, "tau1 * eta must be <= 1");
+  (void)device_ptrs;
+  return LAMP_OK;
+}
+
+static int choose_split(int64_t tout, int64_t tin, int64_t wave, int64_t min_inner) {
+  int best = 1;
+  double best_score = -1.0;
+  int64_t smax = std::min<int64_t>(std::max<int64_t>(tin / std::max<int64_t>(min_inner, 1), 1), 128);
+  for (int s = 1; s <= smax; ++s) {
+    int64_t ctas = tout * s;
+    int64_t waves = (ctas + wave - 1) / wave;
+    double util = (double)ctas / (double)(waves * wave);
+    double score = util - 0.002 * s;
+    if (score > best_score + 1e-12) {
+      best_score = score;
+      best = s;
+    }
+  }
+  return best;
+}
+
+static int build_graph(lamp_ctx* ctx, int slot, int64_t len) {
+  if (ctx->gexec[slot] && ctx->glen[slot] == len) return LAMP_OK;
+  if (ctx->gexec[slot]) {
+    cudaGraphExecDestroy(ctx->gexec[slot]);
+    ctx->gexec[slot] = nullptr;
+  }
+  CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+  for (int64_t i = 0; i < len; ++i) {
+    cudaError_t e = launch_iteration(ctx->in, ctx->k, ctx->w, ctx->g, ctx->prec, ctx->cap);
+    if (e != cudaSuccess) {
+      cudaGraph_t gg;
+      cudaStreamEndCapture(ctx->cap, &gg);
+      if (gg) cudaGraphDestroy(gg);
+      return fail(ctx, LAMP_E_CUDA, "capturing an iteration: %s", cudaGetErrorString(e));
+    }
+  }
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamEndCapture(ctx->cap, &graph));
+  cudaError_t e = cudaGraphInstantiate(&ctx->gexec[slot], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(ctx, LAMP_E_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  ctx->glen[slot] = len;
+  return LAMP_OK;
+}
+
+__global__ void k_ctrl(DevState* dev, int eval_only, double tol, long long tmax_abs, long long tmax_rel, int set) {
+  dev->done = 0;
+  dev->eval_only = eval_only;
+  dev->tol = tol;
+  dev->tmax = tmax_rel >= 0 ? dev->t + tmax_rel : tmax_abs;
+  dev->ticket = 0u;
+  if (set) dev->status = 0;
+}
+
+__global__ void k_set_state(DevState* dev, long long t, double kappa) {
+  dev->t = t;
+  dev->kappa = kappa;
+  dev->done = 0;
+  dev->status = 0;
+  dev->ticket = 0u;
+  dev->t_eval = -1;
+}
+
+static int poll(lamp_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->host_dev, ctx->w.dev, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return LAMP_OK;
+}
+
+static int prime(lamp_ctx* ctx) {
+  // column data of the current buffer, then row shifts from a coarse row-max pass
+  CK(launch_init_state(ctx->in, ctx->k, ctx->w, 0, ctx->stream));
+  CK(launch_prime(ctx->in, ctx->k, ctx->w, ctx->g, ctx->prec, ctx->stream));
+  return LAMP_OK;
+}
+
+static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_params* params, void* stream,
+                       bool owned) {
+  if (!out) return fail(nullptr, LAMP_E_INVALID, "lamp_create: out is null");
+  *out = nullptr;
+  int rc = validate(prob, params, !owned);
+  if (rc) return rc;
+  lamp_ctx* ctx = new lamp_ctx();
+  ctx->params = *params;
+  ctx->prec = params->prec;
+  ctx->stream = (cudaStream_t)stream;
+  auto bail = [&](int code) {
+    lamp_destroy(ctx);
+    return code;
+  };
+  {
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e != cudaSuccess) {
+      fail(nullptr, LAMP_E_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+      delete ctx;
+      return LAMP_E_CUDA;
+    }
+  }
+  prepare_kernels();
+  Consts& k = ctx->k;
+  k.n = prob->n;
+  k.m = prob->m;
+  k.d = prob->kind == LAMP_COST_SQEUCLID ? (int32_t)prob->d : 0;
+  k.kind = prob->kind;
+  k.eta = params->eta;
+  k.alpha = params->alpha;
+  k.clipb = std::tanh(params->beta / 2.0);
+  ctx->log_m = std::log((double)k.m);
+
+  if (cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    fail(nullptr, LAMP_E_CUDA, "cudaStreamCreate failed");
+    delete ctx;
+    return LAMP_E_CUDA;
+  }
+  // inputs
+  Inputs& in = ctx->in;
+  if (owned) {
+    ctx->owned = true;
+    size_t na = prob->kind == LAMP_COST_DENSE ? (size_t)prob->n * prob->m : (size_t)prob->n * prob->d;
+    if ((rc = dalloc(ctx, &ctx->own_a, na))) return bail(rc);
+    if (prob->kind == LAMP_COST_SQEUCLID && (rc = dalloc(ctx, &ctx->own_b, (size_t)prob->m * prob->d)))
+      return bail(rc);
+    if ((rc = dalloc(ctx, &ctx->own_r, (size_t)prob->n))) return bail(rc);
+    if ((rc = dalloc(ctx, &ctx->own_c, (size_t)prob->m))) return bail(rc);
+    cudaError_t e = cudaSuccess;
+    if (prob->kind == LAMP_COST_DENSE) {
+      e = cudaMemcpy2DAsync(ctx->own_a, prob->m * sizeof(float), prob->C, prob->ldc * sizeof(float),
+                            prob->m * sizeof(float), prob->n, cudaMemcpyHostToDevice, ctx->stream);
+    } else {
+      e = cudaMemcpyAsync(ctx->own_a, prob->x, na * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->own_b, prob->y, (size_t)prob->m * prob->d * sizeof(float), cudaMemcpyHostToDevice,
+                            ctx->stream);
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ctx->own_r, prob->r, prob->n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ctx->own_c, prob->c, prob->m * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return bail(fail(ctx, LAMP_E_CUDA, "input copy: %s", cudaGetErrorString(e)));
+    in.C = prob->kind == LAMP_COST_DENSE ? ctx->own_a : nullptr;
+    in.ldc = prob->m;
+    in.x = prob->kind == LAMP_COST_SQEUCLID ? ctx->own_a : nullptr;
+    in.y = ctx->own_b;
+    in.r = ctx->own_r;
+    in.c = ctx->own_c;
+  } else {
+    in.C = prob->C;
+    in.ldc = prob->ldc;
+    in.x = prob->x;
+    in.y = prob->y;
+    in.r = prob->r;
+    in.c = prob->c;
+  }
+
+  // geometry
+  Geometry& g = ctx->g;
+  {
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, ctx->device);
+    if (e != cudaSuccess) return bail(fail(ctx, LAMP_E_CUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(e)));
+    g.sms = prop.multiProcessorCount;
+  }
+  {
+    int bpr = sweep_blocks_per_sm(k, ctx->prec, 0);
+    int bpc = sweep_blocks_per_sm(k, ctx->prec, 1);
+    int64_t to = (k.n + tile_outer(k, ctx->prec) - 1) / tile_outer(k, ctx->prec);
+    int64_t ti = (k.m + tile_inner(k, ctx->prec) - 1) / tile_inner(k, ctx->prec);
+    int64_t tco = (k.m + tile_outer_cols(k, ctx->prec) - 1) / tile_outer_cols(k, ctx->prec);
+    int64_t tci = (k.n + tile_inner_cols(k, ctx->prec) - 1) / tile_inner_cols(k, ctx->prec);
+    g.rows_tiles = (int)to;
+    g.cols_tiles = (int)tco;
+    int min_inner = k.kind == LAMP_COST_DENSE ? 1 : 4;
+    g.rows_split = choose_split(to, ti, (int64_t)g.sms * bpr, min_inner);
+    g.cols_split = choose_split(tco, tci, (int64_t)g.sms * bpc, k.kind == LAMP_COST_DENSE ? 4 : min_inner);
+  }
+
+  // workspace
+  Work& w = ctx->w;
+  const size_t n = (size_t)k.n, m = (size_t)k.m;
+  ctx->rowblocks = (int)((k.n + 255) / 256);
+  int colblocks = (int)((k.m + 255) / 256);
+  size_t gradd = k.kind == LAMP_COST_SQEUCLID ? (size_t)std::min<int64_t>(std::max<int64_t>(k.d, 2), 8) : 2;
+  for (int b = 0; b < 2; ++b) {
+    if ((rc = dalloc(ctx, &w.nu[b], m))) return bail(rc);
+    if ((rc = dalloc(ctx, &w.theta[b], m))) return bail(rc);
+    if ((rc = dalloc(ctx, &w.colq[b], m))) return bail(rc);
+    if ((rc = dalloc(ctx, &w.rowshift[b], n))) return bail(rc);
+  }
+  if ((rc = dalloc(ctx, &w.g2row, n))) return bail(rc);
+  if ((rc = dalloc(ctx, &w.rowpart, (size_t)g.rows_split * std::max<size_t>(2, gradd) * n))) return bail(rc);
+  if ((rc = dalloc(ctx, &w.colpart, (size_t)g.cols_split * std::max<size_t>(3, gradd) * m))) return bail(rc);
+  if ((rc = dalloc(ctx, &w.logZ, n))) return bail(rc);
+  if ((rc = dalloc(ctx, &w.colA, m))) return bail(rc);
+  if ((rc = dalloc(ctx, &w.nx, n))) return bail(rc);
+  if ((rc = dalloc(ctx, &w.ny, m))) return bail(rc);
+  if ((rc = dalloc(ctx, &w.rowred, (size_t)ctx->rowblocks))) return bail(rc);
+  if ((rc = dalloc(ctx, &w.colred, (size_t)colblocks * 3))) return bail(rc);
+  if ((rc = dalloc(ctx, &w.rowmax, (size_t)g.rows_split * 2 * n))) return bail(rc);
+  if ((rc = dalloc(ctx, &w.scratch, (size_t)std::max(3 * 4 * g.sms, 3 * 128)))) return bail(rc);
+  if ((rc = dalloc(ctx, &w.dev, 1))) return bail(rc);
+  {
+    cudaError_t e = cudaMallocHost(&ctx->host_dev, sizeof(DevState));
+    if (e != cudaSuccess) return bail(fail(ctx, LAMP_E_NOMEM, "cudaMallocHost: %s", cudaGetErrorString(e)));
+  }
+  std::memset(ctx->host_dev, 0, sizeof(DevState));
+  ctx->host_dev->t_eval = -1;
+  {
+    cudaError_t e = cudaMemcpyAsync(w.dev, ctx->host_dev, sizeof(DevState), cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return bail(fail(ctx, LAMP_E_CUDA, "init copy: %s", cudaGetErrorString(e)));
+    cudaMemsetAsync(w.nu[0], 0, m * sizeof(double), ctx->stream);
+    cudaMemsetAsync(w.theta[0], 0, m * sizeof(double), ctx->stream);
+    cudaMemsetAsync(w.nu[1], 0, m * sizeof(double), ctx->stream);
+    cudaMemsetAsync(w.theta[1], 0, m * sizeof(double), ctx->stream);
+  }
+
+  // marginals: positive, finite, summing to one (r in Delta^n, c in Delta^m, full support)
+  {
+    cudaError_t e = launch_check_marginals(in, k, w, ctx->stream);
+    if (e != cudaSuccess) return bail(fail(ctx, LAMP_E_CUDA, "marginal check: %s", cudaGetErrorString(e)));
+    std::vector<double> h(3 * 128);
+    e = cudaMemcpyAsync(h.data(), w.scratch, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return bail(fail(ctx, LAMP_E_CUDA, "marginal check: %s", cudaGetErrorString(e)));
+    for (int which = 0; which < 2; ++which) {
+      double S = 0, M = INFINITY, B = 0;
+      for (int b = 0; b < 64; ++b) {
+        S += h[which * 192 + 3 * b];
+        M = std::min(M, h[which * 192 + 3 * b + 1]);
+        B = std::max(B, h[which * 192 + 3 * b + 2]);
+      }
+      if (B != 0.0 || !(M > 0.0) || std::fabs(S - 1.0) > 1e-9)
+        return bail(fail(ctx, LAMP_E_INVALID, "%s must be positive, finite and sum to 1 (sum-1=%.3e, min=%.3e)",
+                         which ? "c" : "r", S - 1.0, M));
+    }
+  }
+  // H(r) on the host needs r: copy it once (O(n))
+  {
+    std::vector<double> hr(n);
+    cudaError_t e = cudaMemcpyAsync(hr.data(), in.r, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return bail(fail(ctx, LAMP_E_CUDA, "copy r: %s", cudaGetErrorString(e)));
+    double H = 0.0;
+    for (double v : hr) H -= v * std::log(v);
+    ctx->Hr = H;
+  }
+
+  // cost scale and K = ||C||_inf of the cost the kernels use
+  {
+    cudaError_t e = launch_norms(in, k, w, ctx->stream);
+    if (e != cudaSuccess) return bail(fail(ctx, LAMP_E_CUDA, "norms: %s", cudaGetErrorString(e)));
+    bool need_K = !(params->K > 0.0);
+    bool need_scale = prob->kind == LAMP_COST_SQEUCLID && prob->cost_scale < 0.0;
+    double s = prob->kind == LAMP_COST_SQEUCLID ? (prob->cost_scale > 0.0 ? prob->cost_scale : 1.0) : 1.0;
+    double Dmax = NAN, Dmin = NAN;
+    if (need_K || need_scale || prob->kind == LAMP_COST_DENSE) {
+      k.K = 1.0;
+      k.s = s;
+      e = launch_kmax(in, k, w, g, ctx->prec, ctx->stream);
+      if (e != cudaSuccess) return bail(fail(ctx, LAMP_E_CUDA, "K pass: %s", cudaGetErrorString(e)));
+      if (prob->kind == LAMP_COST_DENSE) {
+        std::vector<double> h(3 * 4 * g.sms);
+        e = cudaMemcpyAsync(h.data(), w.scratch, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return bail(fail(ctx, LAMP_E_CUDA, "K pass: %s", cudaGetErrorString(e)));
+        Dmax = -INFINITY;
+        Dmin = INFINITY;
+        double bad = 0;
+        for (int b = 0; b < 4 * g.sms; ++b) {
+          Dmax = std::max(Dmax, h[3 * b]);
+          Dmin = std::min(Dmin, h[3 * b + 1]);
+          bad = std::max(bad, h[3 * b + 2]);
+        }
+        if (bad != 0.0 || !(Dmin >= 0.0))
+          return bail(fail(ctx, LAMP_E_INVALID, "C must be finite and >= 0 (min %.3e)", Dmin));
+      } else {
+        std::vector<float> h((size_t)g.rows_split * 2 * n);
+        e = cudaMemcpyAsync(h.data(), w.rowmax, h.size() * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return bail(fail(ctx, LAMP_E_CUDA, "K pass: %s", cudaGetErrorString(e)));
+        float mx = -INFINITY, mnneg = -INFINITY;
+        for (int sp = 0; sp < g.rows_split; ++sp)
+          for (size_t i = 0; i < n; ++i) {
+            mx = std::max(mx, h[(sp * 2 + 0) * n + i]);
+            mnneg = std::max(mnneg, h[(sp * 2 + 1) * n + i]);
+          }
+        Dmax = mx;
+        Dmin = -(double)mnneg;
+        if (!std::isfinite(Dmax)) return bail(fail(ctx, LAMP_E_INVALID, "points must be finite"));
+      }
+    }
+    if (need_scale) {
+      if (!(Dmax > 0.0)) return bail(fail(ctx, LAMP_E_INVALID, "cost_scale < 0 needs a positive maximum cost"));
+      s = 1.0 / Dmax;
+    }
+    k.s = s;
+    double Kc = prob->kind == LAMP_COST_DENSE ? Dmax : s * std::max(Dmax, -Dmin);
+    k.K = need_K ? Kc : params->K;
+    if (!(k.K > 0.0) || !std::isfinite(k.K))
+      return bail(fail(ctx, LAMP_E_INVALID, "||C||_inf must be positive and finite (got %g)", k.K));
+  }
+  k.tau1 = params->tau1 > 0.0 ? params->tau1 : 1.0 / (2.0 * k.K);
+  k.tau2 = params->tau2 > 0.0 ? params->tau2 : 1.0 / (2.0 * k.K);
+  if (k.tau1 * k.eta > 1.0) return bail(fail(ctx, LAMP_E_INVALID, "tau1 * eta must be <= 1"));
+
+  // offset bound factor W: |Bq_j| + |Rq_i| <= lambda W + 128 (see lamp_common.cuh)
+  if (k.kind == COST_DENSE) {
+    k.W = 5.0 * k.K;
+    k.rnx = 0.0;
+  } else {
+    std::vector<double> hx(n), hy(m), hr(n);
+    cudaError_t e = cudaMemcpyAsync(hx.data(), w.nx, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hy.data(), w.ny, m * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hr.data(), in.r, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return bail(fail(ctx, LAMP_E_CUDA, "norm copy: %s", cudaGetErrorString(e)));
+    double nxm = 0, nym = 0, rnx = 0;
+    for (size_t i = 0; i < n; ++i) {
+      nxm = std::max(nxm, hx[i]);
+      rnx += hr[i] * hx[i];
+    }
+    for (size_t j = 0; j < m; ++j) nym = std::max(nym, hy[j]);
+    k.W = k.s * (nxm + 3.0 * nym) + 4.0 * k.K + 2.0 * k.s * (nxm + nym);
+    k.rnx = k.s * rnx;
+  }
+
+  if ((rc = prime(ctx))) return bail(rc);
+  {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return bail(fail(ctx, LAMP_E_CUDA, "create: %s", cudaGetErrorString(e)));
+  }
+  *out = ctx;
+  return LAMP_OK;
+}
+
+extern "C" int lamp_create(lamp_ctx** out, const lamp_problem* prob, const lamp_params* params, void* stream) {
+  return create_impl(out, prob, params, stream, false);
+}
+
+extern "C" int lamp_create_owned(lamp_ctx** out, const lamp_problem* prob, const lamp_params* params,
+                                 void* stream) {
+  return create_impl(out, prob, params, stream, true);
+}
+
+static int run_graph(lamp_ctx* ctx, int slot, int64_t len) {
+  int rc = build_graph(ctx, slot, len);
+  if (rc) return rc;
+  CK(cudaGraphLaunch(ctx->gexec[slot], ctx->stream));
+  return LAMP_OK;
+}
+
+static void fill_result(lamp_ctx* ctx, lamp_result* out) {
+  if (!out) return;
+  const DevState& d = *ctx->host_dev;
+  out->iters = d.t;
+  out->infeas = d.res;
+  out->obj_CX = d.costA;
+  out->kappa = d.kappa;
+  out->K = ctx->k.K;
+  out->status = d.status;
+}
+
+extern "C" int lamp_solve(lamp_ctx* ctx, lamp_result* out) {
+  if (!ctx) return fail(nullptr, LAMP_E_INVALID, "lamp_solve: null context");
+  k_ctrl<<<1, 1, 0, ctx->stream>>>(ctx->w.dev, 0, ctx->params.tol, ctx->params.max_iter, -1, 0);
+  CK(cudaGetLastError());
+  const int64_t L = ctx->params.check_every;
+  for (;;) {
+    int rc = run_graph(ctx, 1, L);
+    if (rc) return rc;
+    if ((rc = poll(ctx))) return rc;
+    if (ctx->host_dev->done) break;
+  }
+  fill_result(ctx, out);
+  const DevState& d = *ctx->host_dev;
+  if (d.status != 0) {
+    if (out) out->status = LAMP_E_NUMERIC;
+    return fail(ctx, LAMP_E_NUMERIC, "non-finite or out-of-range sum at iteration %lld", (long long)d.t);
+  }
+  if (!(d.res <= ctx->params.tol)) {
+    if (out) out->status = LAMP_E_NOT_CONVERGED;
+    return fail(ctx, LAMP_E_NOT_CONVERGED, "max_iter reached (t=%lld, infeasibility %.3e)", (long long)d.t, d.res);
+  }
+  return LAMP_OK;
+}
+
+extern "C" int lamp_iterate(lamp_ctx* ctx, int64_t iters) {
+  if (!ctx) return fail(nullptr, LAMP_E_INVALID, "lamp_iterate: null context");
+  if (iters < 0) return fail(ctx, LAMP_E_INVALID, "iters must be >= 0");
+  if (iters == 0) return LAMP_OK;
+  k_ctrl<<<1, 1, 0, ctx->stream>>>(ctx->w.dev, 0, -1.0, 0, iters, 0);
+  CK(cudaGetLastError());
+  const int64_t L = ctx->params.check_every;
+  int64_t left = iters;
+  while (left >= L && L > 1) {
+    int rc = run_graph(ctx, 1, L);
+    if (rc) return rc;
+    left -= L;
+  }
+  while (left > 0) {
+    int rc = run_graph(ctx, 0, 1);
+    if (rc) return rc;
+    --left;
+  }
+  return LAMP_OK;
+}
+
+static int evaluate(lamp_ctx* ctx) {
+  k_ctrl<<<1, 1, 0, ctx->stream>>>(ctx->w.dev, 1, -1.0, 0, 0, 0);
+  CK(cudaGetLastError());
+  int rc = run_graph(ctx, 0, 1);
+  if (rc) return rc;
+  return poll(ctx);
+}
+
+extern "C" int lamp_objective(lamp_ctx* ctx, double out[8]) {
+  if (!ctx || !out) return fail(ctx, LAMP_E_INVALID, "lamp_objective: null argument");
+  int rc = evaluate(ctx);
+  if (rc) return rc;
+  const DevState& d = *ctx->host_dev;
+  const Consts& k = ctx->k;
+  // H(X) = H(r) + kappa <C,X> + 2 K kappa <col(X), nu> + <r, log Z>  (App. D identity, any kappa)
+  double H = ctx->Hr + d.kappa * d.costA + 2.0 * k.K * d.kappa * d.colnu + d.rlogZ;
+  out[0] = d.costA;
+  out[1] = d.res;
+  out[2] = 0.0;  // row(X^t) = r by construction of p^{eta}(nu) (Eq. row_feasible)
+  out[3] = H;
+  out[4] = d.costA + 2.0 * k.K * d.res - k.eta * H;
+  out[5] = (k.eta == 0.0 && d.t >= 1) ? 4.0 * k.K * d.res + 2.0 * k.K * ctx->log_m / (double)d.t : NAN;
+  out[6] = NAN;
+  out[7] = k.K;
+  if (d.status != 0) return fail(ctx, LAMP_E_NUMERIC, "non-finite or out-of-range sum");
+  return LAMP_OK;
+}
+
+extern "C" int lamp_grad(lamp_ctx* ctx, float* dx, float* dy) {
+  if (!ctx) return fail(nullptr, LAMP_E_INVALID, "lamp_grad: null context");
+  if (ctx->k.kind != COST_SQEUCLID) return fail(ctx, LAMP_E_UNSUPPORTED, "lamp_grad needs LAMP_COST_SQEUCLID");
+  if (ctx->k.d > 8) return fail(ctx, LAMP_E_UNSUPPORTED, "lamp_grad supports d <= 8 in this build");
+  int rc = evaluate(ctx);
+  if (rc) return rc;
+  CK(launch_grad(ctx->in, ctx->k, ctx->w, ctx->g, ctx->prec, dx, dy, ctx->stream));
+  return LAMP_OK;
+}
+
+extern "C" int lamp_get_state(lamp_ctx* ctx, double* nu, double* theta, double* logZ, double* kappa, int64_t* t,
+                              float* row_shifts) {
+  if (!ctx) return fail(nullptr, LAMP_E_INVALID, "lamp_get_state: null context");
+  int rc = poll(ctx);
+  if (rc) return rc;
+  const DevState& d = *ctx->host_dev;
+  const int cur = d.cur;
+  if (nu) CK(cudaMemcpyAsync(nu, ctx->w.nu[cur], ctx->k.m * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  if (theta)
+    CK(cudaMemcpyAsync(theta, ctx->w.theta[cur], ctx->k.m * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  if (logZ) CK(cudaMemcpyAsync(logZ, ctx->w.logZ, ctx->k.n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  if (row_shifts)
+    CK(cudaMemcpyAsync(row_shifts, ctx->w.rowshift[cur], ctx->k.n * sizeof(float2), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (logZ && d.t_eval != d.t)
+    for (int64_t i = 0; i < ctx->k.n; ++i) logZ[i] = NAN;
+  if (kappa) *kappa = d.kappa;
+  if (t) *t = d.t;
+  return LAMP_OK;
+}
+
+extern "C" int lamp_set_state(lamp_ctx* ctx, const double* nu, const double* theta, double kappa, int64_t t,
+                              const float* row_shifts) {
+  if (!ctx || !nu || !theta) return fail(ctx, LAMP_E_INVALID, "lamp_set_state: null argument");
+  if (!(kappa >= 0.0) || !std::isfinite(kappa) || t < 0) return fail(ctx, LAMP_E_INVALID, "bad kappa or t");
+  for (int64_t j = 0; j < ctx->k.m; ++j)
+    if (!(std::fabs(nu[j]) < 1.0) || !(std::fabs(theta[j]) < 1.0))
+      return fail(ctx, LAMP_E_INVALID, "nu and theta must lie in (-1, 1)");
+  int rc = poll(ctx);
+  if (rc) return rc;
+  const int cur = ctx->host_dev->cur;
+  CK(cudaMemcpyAsync(ctx->w.nu[cur], nu, ctx->k.m * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->w.theta[cur], theta, ctx->k.m * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  k_set_state<<<1, 1, 0, ctx->stream>>>(ctx->w.dev, t, kappa);
+  CK(cudaGetLastError());
+  if (row_shifts) {
+    for (int64_t i = 0; i < 2 * ctx->k.n; ++i)
+      if (!std::isfinite(row_shifts[i])) return fail(ctx, LAMP_E_INVALID, "row_shifts must be finite");
+    CK(launch_init_state(ctx->in, ctx->k, ctx->w, 0, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->w.rowshift[cur], row_shifts, ctx->k.n * sizeof(float2), cudaMemcpyHostToDevice,
+                       ctx->stream));
+  } else if ((rc = prime(ctx))) {
+    return rc;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return LAMP_OK;
+}
+
+extern "C" int lamp_step_host(lamp_ctx* ctx, const float* C_or_x, const float* y, const double* r, const double* c,
+                              int64_t iters, double* infeas_out, double* nu_out) {
+  if (!ctx) return fail(nullptr, LAMP_E_INVALID, "lamp_step_host: null context");
+  if (!ctx->owned) return fail(ctx, LAMP_E_INVALID, "lamp_step_host needs a context from lamp_create_owned");
+  const Consts& k = ctx->k;
+  if (!C_or_x || !r || !c || (k.kind == COST_SQEUCLID && !y)) return fail(ctx, LAMP_E_INVALID, "null input");
+  size_t na = k.kind == COST_DENSE ? (size_t)k.n * k.m : (size_t)k.n * k.d;
+  CK(cudaMemcpyAsync(ctx->own_a, C_or_x, na * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  if (k.kind == COST_SQEUCLID)
+    CK(cudaMemcpyAsync(ctx->own_b, y, (size_t)k.m * k.d * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->own_r, r, k.n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->own_c, c, k.m * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  int rc = lamp_iterate(ctx, iters);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(&ctx->host_dev->res, &ctx->w.dev->res, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  if (nu_out) {
+    // the buffer parity is only known on the device; copy both halves' candidate after reading cur
+    CK(cudaMemcpyAsync(&ctx->host_dev->cur, &ctx->w.dev->cur, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpyAsync(nu_out, ctx->w.nu[ctx->host_dev->cur], k.m * sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (infeas_out) *infeas_out = ctx->host_dev->res;
+  return LAMP_OK;
+}
+
+extern "C" int64_t lamp_launches_per_iteration(const lamp_ctx* ctx) {
+  if (!ctx) return 0;
+  return launches_per_iteration(ctx->k, ctx->prec);
+}
+
+extern "C" const char* lamp_last_error(const lamp_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+extern "C" void lamp_destroy(lamp_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (int s = 0; s < 2; ++s)
+    if (ctx->gexec[s]) cudaGraphExecDestroy(ctx->gexec[s]);
+  for (void* p : ctx->allocs) cudaFree(p);
+  if (ctx->host_dev) cudaFreeHost(ctx->host_dev);
+  if (ctx->cap) cudaStreamDestroy(ctx->cap);
+  delete ctx;
+}

@@ -1,0 +1,217 @@
+// Shared definitions of the LAMP CUDA library (device side + host launch glue).
+//
+// Notation (arXiv 2511.11359):
+//   K = ||C||_inf, kappa_t = 1/eta_t (kappa_0 = 0), s = cost scale.
+//   Stream A of iteration t is (kappa_t, nu^t)            -> X^t       (Alg. 2, thetabar step)
+//   Stream B of iteration t is (kappa_{t+1}, nubar^{t+1}) -> Xbar^{t+1} (Alg. 2, thetahat step)
+//   Both only depend on (nu^t, theta^t, kappa_t), so one pass over the (i,j)
+//   pairs serves both streams.
+//
+// Compensated base-2 exponent.  With lambda = kappa * log2(e), the exponent of
+// p^{eta}(nu)_ij is, in base 2 and up to the row normaliser,
+//     s2_ij = -lambda (C_ij + 2K nu_j).
+// The kernels evaluate it as v_ij = a z_ij - Bq_j - Rq_i where
+//   DENSE:    z = C_ij,          a = -lambda,   Bcol_j = lambda 2K nu_j,          Rrow_i = M_i
+//   SQEUCLID: z = x_i . y_j,     a = 2 lambda s, Bcol_j = lambda (s|y_j|^2 + 2K nu_j),
+//                                               Rrow_i = lambda s |x_i|^2 + M_i
+// with M_i a per-row shift (a running estimate of log2 of the row maximum).
+// Bq_j and Rq_i are Bcol_j, Rrow_i rounded to a power-of-two grid g chosen so
+// that |Bq| + |Rq| < 2^23 g: their float32 sum is then exact, the product a z
+// is exact inside the FMA, and a = ah + al (two floats) keeps kappa's float64
+// precision.  v therefore carries one float32 rounding relative to |v| itself
+// (|v| = O(1) for the entries that matter), instead of relative to
+// lambda |C| = O(t), which is what a naive float32 exponent would give at
+// eta = 0 where kappa_t = t/(2K) grows without bound (Section 3.2).
+// The sub-grid remainder Br_j = Bcol_j - Bq_j enters as the factor
+// w_j = 2^{-Br_j} (row sums) or as a per-column factor after the sum (column sums).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lamp {
+
+constexpr double kLog2e = 1.4426950408889634074;
+constexpr double kLn2 = 0.69314718055994530942;
+
+enum CostKind : int { COST_DENSE = 0, COST_SQEUCLID = 1 };
+
+// Problem constants, fixed for the lifetime of a context (passed by value).
+struct Consts {
+  int64_t n, m;
+  int32_t d, kind;
+  double K;          // ||C||_inf of the cost in use
+  double s;          // cost scale (1 for DENSE)
+  double tau1, tau2, eta, alpha;
+  double clipb;      // tanh(beta/2)
+  double W;          // bound factor for the exponent offsets: |Bq|+|Rq| <= lambda*W + 128
+  double rnx;        // sum_i r_i s |x_i|^2 (SQEUCLID cost bookkeeping), 0 for DENSE
+};
+
+// Parameters of one iteration's sweeps, derived from kappa_t alone.
+struct SweepParams {
+  double kapA, kapB;   // kappa_t, kappa_{t+1}
+  double lamA, lamB;   // kappa * log2(e)
+  double aA, aB;       // float64 exponent multipliers of z
+  float ahA, alA, ahB, alB;  // a = ah + al, both float32
+  double g;            // offset grid (power of two)
+};
+
+__host__ __device__ inline double kappa_next(double kap, const Consts& k) {
+  // 1/eta_{t+1} = tau1 + (1/eta_t)(1 - tau1 eta)   (Alg. 2, Section 3.2)
+  return k.tau1 + kap * (1.0 - k.tau1 * k.eta);
+}
+
+__host__ __device__ inline double pow2i(int e) {
+  // exact 2^e for |e| < 1000
+  double r = 1.0;
+  double b = e >= 0 ? 2.0 : 0.5;
+  int q = e >= 0 ? e : -e;
+  while (q) {
+    if (q & 1) r *= b;
+    b *= b;
+    q >>= 1;
+  }
+  return r;
+}
+
+__host__ __device__ inline SweepParams make_sweep_params(double kap, const Consts& k) {
+  SweepParams p;
+  p.kapA = kap;
+  p.kapB = kappa_next(kap, k);
+  p.lamA = p.kapA * kLog2e;
+  p.lamB = p.kapB * kLog2e;
+  if (k.kind == COST_DENSE) {
+    p.aA = -p.lamA;
+    p.aB = -p.lamB;
+  } else {
+    p.aA = 2.0 * p.lamA * k.s;
+    p.aB = 2.0 * p.lamB * k.s;
+  }
+  p.ahA = (float)p.aA;
+  p.alA = (float)(p.aA - (double)p.ahA);
+  p.ahB = (float)p.aB;
+  p.alB = (float)(p.aB - (double)p.ahB);
+  double lmax = p.lamA > p.lamB ? p.lamA : p.lamB;
+  double bound = lmax * k.W + 128.0;
+  // smallest e with 2^e >= bound, then g = 2^(e-23)
+  int e = 0;
+  double v = 1.0;
+  while (v < bound) { v *= 2.0; ++e; }
+  p.g = pow2i(e - 23);
+  return p;
+}
+
+// round-to-nearest multiple of the power-of-two grid g, exact in float64
+__host__ __device__ inline double quantize(double x, double g) {
+#ifdef __CUDA_ARCH__
+  return rint(x / g) * g;
+#else
+  return __builtin_rint(x / g) * g;
+#endif
+}
+
+#ifdef __CUDACC__
+// 2^x with the SFU (MUFU.EX2), flush-to-zero
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Knuth's branch-free TwoSum: s + e == a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// accumulate x into the float-float pair (hi, lo)
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
+  float s, e;
+  two_sum(hi, x, s, e);
+  hi = s;
+  lo += e;
+}
+#endif
+
+// Device-resident control block of one context.
+struct DevState {
+  long long t;        // iteration index of the current state
+  double kappa;       // kappa_t
+  int cur;            // which of the two state buffers holds state t
+  int done;           // set: the remaining launches of a device loop return at once
+  int status;         // 0 or LAMP_E_NUMERIC
+  int eval_only;      // 1: compute the pass but never apply the update
+  double tol;         // stop when res <= tol
+  long long tmax;     // stop when t >= tmax
+  unsigned int ticket;  // last-block counter of the column finalize kernel
+  unsigned int pad;
+  // results for the last evaluated X^t
+  long long t_eval;
+  double kappa_eval;
+  double res;         // ||col(X^t) - c||_1 (+ ||row(X^t) - r||_1 = 0 by construction)
+  double costA;       // <C, X^t>
+  double colnu;       // <col(X^t), nu^t>
+  double rlogZ;       // <r, log Z^t>
+};
+
+// Device buffers of one context (all owned by the context).
+struct Work {
+  double* nu[2];
+  double* theta[2];
+  float4* colq[2];     // per column {BqA, wA, BqB, wB}
+  float2* rowshift[2]; // per row {RqA, RqB}
+  float4* g2row;       // per row {RqA, qA, RqB, qB} for the column sweep
+  double* rowpart;     // [splits_rows][2][n] partial row sums
+  double* colpart;     // [splits_cols][3][m] partial column sums (A, B, cost-weighted A)
+  double* logZ;        // [n] natural-log normalisers of X^t
+  double* colA;        // [m] col(X^t)
+  double* nx;          // [n] |x_i|^2 (SQEUCLID)
+  double* ny;          // [m] |y_j|^2 (SQEUCLID)
+  double* rowred;      // [rowfin blocks] partial <r, log Z>
+  double* colred;      // [colfin blocks][3] partial (res, cost, colnu)
+  float* rowmax;       // [splits_rows][2][n] partial row maxima (prime pass)
+  double* scratch;     // small reduction scratch (K pass, marginal checks)
+  DevState* dev;
+};
+
+// Launch geometry chosen at create time.
+struct Geometry {
+  int sms;
+  int rows_split;   // inner splits of the row sweep
+  int cols_split;   // inner splits of the column sweep
+  int rows_tiles;   // outer tiles of the row sweep
+  int cols_tiles;   // outer tiles of the column sweep
+};
+
+struct Inputs {
+  const float* C;
+  int64_t ldc;
+  const float* x;
+  const float* y;
+  const double* r;
+  const double* c;
+};
+
+// ---- launchers (lamp_kernels.cu) ----
+cudaError_t launch_norms(const Inputs& in, const Consts& k, const Work& w, cudaStream_t st);
+cudaError_t launch_kmax(const Inputs& in, const Consts& k, const Work& w, const Geometry& g,
+                        int prec, cudaStream_t st);
+cudaError_t launch_check_marginals(const Inputs& in, const Consts& k, const Work& w, cudaStream_t st);
+cudaError_t launch_init_state(const Inputs& in, const Consts& k, const Work& w, int zero, cudaStream_t st);
+cudaError_t launch_prime(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
+                         cudaStream_t st);
+cudaError_t launch_iteration(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
+                             cudaStream_t st);
+void prepare_kernels();
+int tile_outer_cols(const Consts& k, int prec);
+int tile_inner_cols(const Consts& k, int prec);
+cudaError_t launch_grad(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
+                        float* dx, float* dy, cudaStream_t st);
+int launches_per_iteration(const Consts& k, int prec);
+int sweep_blocks_per_sm(const Consts& k, int prec, int which);
+int tile_outer(const Consts& k, int prec);
+int tile_inner(const Consts& k, int prec);
+
+}  // namespace lamp

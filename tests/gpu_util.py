@@ -1,0 +1,63 @@
+"""Helpers shared by the GPU parity tests: build solvers on identical seeded inputs
+and run the FP64 oracle beside them.
+
+Tolerances (the targets stated for this path, written out once here):
+  POT_TOL   potentials nu, theta (in (-1, 1)): max |gpu - oracle| <= 1e-5
+  LOGZ_TOL  log Z: |gpu - oracle| <= 1e-5 (1 + |log Z|)
+  OBJ_TOL   <C, X>: relative 1e-6
+  GRAD_TOL  gradients: relative (max-norm) 1e-4
+"""
+import numpy as np
+
+import oracle as O
+import workloads as W
+
+POT_TOL = 1e-5
+LOGZ_TOL = 1e-5
+OBJ_TOL = 1e-6
+GRAD_TOL = 1e-4
+
+
+def dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def oracle_cost(w):
+    """(C64, cost_scale for the GPU, K): the oracle's float64 cost of the workload,
+    the positive scale that makes the GPU solve the same cost, and ||C||_inf."""
+    if w.kind == "dense":
+        C = np.asarray(w.C, dtype=np.float64)
+        return C, 1.0, float(C.max())
+    D = O.sqeuclid_cost(w.x, w.y)
+    s = w.cost_scale
+    if s < 0:
+        s = 1.0 / D.max()
+    elif s == 0:
+        s = 1.0
+    C = D * s
+    return C, s, float(C.max())
+
+
+def gpu_solver(w, K=None, scale=None, **params):
+    import paper_2511_11359_gb300 as L
+
+    C, s, Kref = oracle_cost(w)
+    K = Kref if K is None else K
+    r, c = dev(w.r), dev(w.c)
+    if w.kind == "dense":
+        return L.Lamp(r, c, C=dev(w.C), K=K, **params), C, K
+    return L.Lamp(r, c, x=dev(w.x), y=dev(w.y), cost_scale=s if scale is None else scale, K=K, **params), C, K
+
+
+def assert_pot_close(st, ref, tol=POT_TOL, what=""):
+    dn = np.abs(st["nu"] - ref.nu).max()
+    dt = np.abs(st["theta"] - ref.theta).max()
+    assert dn <= tol and dt <= tol, f"{what}: |dnu|={dn:.3e} |dtheta|={dt:.3e} (tol {tol:.0e})"
+
+
+def assert_logZ_close(lz, ref, tol=LOGZ_TOL, what=""):
+    err = np.abs(lz - ref) / (1.0 + np.abs(ref))
+    assert np.all(np.isfinite(lz)), what
+    assert err.max() <= tol, f"{what}: log Z rel err {err.max():.3e}"
