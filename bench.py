@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Benchmark of the LAMP hot path on synthetic workloads shaped like the paper's.
+
+A step is one LAMP iteration (Alg. 2): the fused row sweep, row finalize, fused
+column sweep and column finalize over all n x m cost entries, both streams.
+The default workload is the high-dimensional one: n = m = 2^15 points in R^64,
+x ~ N(0, I), y ~ N(0.5 1, I), uniform marginals, eta = 0, squared Euclidean
+cost generated on the fly.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--prec fp32|bf16_tc]
+    python bench.py --impl reference ...     # the FP64 CPU oracle on a bounded sample
+
+Prints ONE JSON line (rank 0).  value = n*m*K / (device seconds of the K steps),
+summed over ranks (each rank solves its own replica: weak scaling, no collective
+on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cost-entries/s/iter and time-to-infeasibility≤1e-6 at n=m=2^15 (BF16-TC vs plain FP32)"
+UNIT = "cost-entries/s"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+def make_workload(name: str, rank: int, n=None):
+    import workloads as W
+
+    if n is not None:  # reduced sizes, for profiling captures only
+        if name == "highdim":
+            return W.highdim(n=n, seed=33 + rank)
+        if name == "plain_2d":
+            return W.plain_2d(n=n, seed=11 + rank)
+        if name == "image_grid":
+            return W.image_grid(side=int(round(n ** 0.5)), seed=22 + rank)
+        if name == "diffloss":
+            return W.diffloss(n=n, seed=44 + rank)
+        if name == "largescale":
+            return W.largescale(n=n, seed=55 + rank)
+    if name == "highdim":
+        return W.highdim(seed=33 + rank)
+    if name == "plain_2d":
+        return W.plain_2d(seed=11 + rank)
+    if name == "image_grid":
+        return W.image_grid(seed=22 + rank)
+    if name == "diffloss":
+        return W.diffloss(seed=44 + rank)
+    if name == "largescale":
+        return W.largescale(seed=55 + rank)
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm_, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm_)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(w, max_points: int):
+    """A bounded sample of the same workload for the CPU oracle: the first
+    max_points sources and targets, marginals renormalised."""
+    import oracle as O
+
+    ns = min(w.n, max_points)
+    ms = min(w.m, max_points)
+    r = w.r[:ns] / w.r[:ns].sum()
+    c = w.c[:ms] / w.c[:ms].sum()
+    if w.kind == "dense":
+        C = np.asarray(w.C[:ns, :ms], dtype=np.float64)
+    else:
+        C = O.sqeuclid_cost(w.x[:ns], w.y[:ms])
+        if w.cost_scale < 0:
+            C /= C.max()
+        elif w.cost_scale > 0:
+            C *= w.cost_scale
+    return C, r, c, ns, ms
+
+
+def time_oracle(w, seconds: float, max_points: int, min_iters: int = 2, fixed_iters: int = 0):
+    """Time oracle iterations (Alg. 2, FP64 NumPy) on a bounded sample; returns
+    (entries/s/iter, iterations, seconds, sample description)."""
+    import oracle as O
+
+    C, r, c, ns, ms = oracle_sample(w, max_points)
+    P = O.LampParams(eta=w.eta)
+    K, tau1, tau2 = O.resolve_params(C, P)
+    ca = O.calpha_of(c, P.alpha)
+    st = O.lamp_initial_state(ms)
+    st, _ = O.lamp_step(C, r, c, K, tau1, tau2, P.eta, ca, P.beta, st)  # warm-up
+    it = 0
+    t0 = time.perf_counter()
+    while True:
+        st, _ = O.lamp_step(C, r, c, K, tau1, tau2, P.eta, ca, P.beta, st)
+        it += 1
+        el = time.perf_counter() - t0
+        if fixed_iters:
+            if it >= fixed_iters:
+                break
+        elif it >= min_iters and el >= seconds:
+            break
+    el = time.perf_counter() - t0
+    desc = (f"{it} Alg. 2 iterations of the FP64 NumPy oracle on the first {ns} x {ms} supports of the "
+            f"{w.name} workload (cost matrix precomputed, not timed)")
+    return ns * ms * it / el, it, el, desc
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 CPU oracle as it stands, on the host cores."""
+    if rank != 0:
+        return
+    w = make_workload(args.workload, 0, args.n)
+    _, it, el, desc = time_oracle(w, 0, args.cpu_points, fixed_iters=args.warmup)  # warm-up steps
+    value, it, el, desc = time_oracle(w, 0, args.cpu_points, fixed_iters=args.steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / it, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": w.n, "m": w.m, "d": w.d, "eta": w.eta,
+                   "sample": f"{min(w.n, args.cpu_points)}x{min(w.m, args.cpu_points)}"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, rank, world):
+    import torch
+    import paper_2511_11359_gb300 as L
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    devc = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=devc)
+
+    w = make_workload(args.workload, rank, args.n)
+    n, m = w.n, w.m
+    r = torch.from_numpy(w.r).to(devc)
+    c = torch.from_numpy(w.c).to(devc)
+    params = dict(eta=w.eta, tol=w.tol, check_every=args.check_every, prec=args.prec)
+    if w.kind == "dense":
+        C = torch.from_numpy(w.C).to(devc)
+        solver = L.Lamp(r, c, C=C, **params)
+        h2d_bytes = w.C.nbytes + w.r.nbytes + w.c.nbytes
+        flops_per_entry = 0
+        bytes_per_entry = 4
+    else:
+        x = torch.from_numpy(w.x).to(devc)
+        y = torch.from_numpy(w.y).to(devc)
+        solver = L.Lamp(r, c, x=x, y=y, cost_scale=w.cost_scale, **params)
+        h2d_bytes = w.x.nbytes + w.y.nbytes + w.r.nbytes + w.c.nbytes
+        flops_per_entry = 2 * w.d
+        bytes_per_entry = 0
+    stream = torch.cuda.current_stream()
+    launches = solver.launches_per_iteration()
+
+    # L2 flush buffer (larger than the 129 MB L2), written between timed steps
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=devc)
+
+    for _ in range(args.warmup):
+        solver.iterate(1)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        solver.iterate(1)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    # per-kernel device times, measured with events between the launches
+    kern_ms = solver.time_kernels(max(3, min(args.steps, 10)))
+    clocks = sampler.stop()
+    t_dev = torch.tensor([total_ms], dtype=torch.float64, device=devc)
+    if dist:
+        dist.all_reduce(t_dev, op=dist.ReduceOp.MAX)
+    total_ms = float(t_dev.item())
+    value = world * n * m * args.steps / (total_ms / 1e3)
+
+    # end to end through the C ABI with host buffers: every step uploads the inputs
+    # from pinned host memory, runs one iteration and reads back nu and the residual
+    e2e = None
+    if args.e2e_steps > 0:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        if w.kind == "dense":
+            hst = L.LampHost(w.r, w.c, C=w.C, **params)
+            a_h, b_h = pin(w.C), None
+        else:
+            hst = L.LampHost(w.r, w.c, x=w.x, y=w.y, cost_scale=w.cost_scale, **params)
+            a_h, b_h = pin(w.x), pin(w.y)
+        r_h, c_h = pin(w.r), pin(w.c)
+        nu_h = torch.empty(m, dtype=torch.float64).pin_memory().numpy()
+        for _ in range(2):
+            hst.step(1, a_h, b_h, r_h, c_h, nu_out=nu_h)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            hst.step(1, a_h, b_h, r_h, c_h, nu_out=nu_h)
+        el = time.perf_counter() - t0
+        hst.close()
+        e2e = {"value": world * n * m * args.e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d_bytes),
+               "d2h_bytes_per_step": int(8 + 8 * m), "steps": args.e2e_steps}
+
+    info = {}
+    if rank == 0 and args.ttt:
+        # time to infeasibility <= tol from the Alg. 2 start, through lamp_solve
+        s2 = L.Lamp(r, c, x=x, y=y, cost_scale=w.cost_scale, max_iter=args.ttt_max_iter,
+                    **params) if w.kind != "dense" else L.Lamp(r, c, C=C, max_iter=args.ttt_max_iter, **params)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = s2.solve()
+        el = time.perf_counter() - t0
+        info["time_to_tol"] = {"seconds": el, "iters": res["iters"], "infeas": res["infeas"],
+                               "converged": res["converged"], "tol": w.tol}
+        s2.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks, src = load_peaks()
+    sweep_ms = max(kern_ms[0], kern_ms[2])
+    dom = 0 if kern_ms[0] >= kern_ms[2] else 2
+    if bytes_per_entry:
+        achieved = n * m * bytes_per_entry / (kern_ms[dom] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None}
+    else:
+        mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        peak = sms * 128 * 2 * mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flop x max SM clock
+        achieved = n * m * flops_per_entry / (kern_ms[dom] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "what": "fp32 x.y FMA of the " + ("row" if dom == 0 else "column") + " sweep",
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz"}
+    roof["kernel_ms"] = {"row_sweep": kern_ms[0], "row_fin": kern_ms[1], "col_sweep": kern_ms[2],
+                         "col_fin": kern_ms[3]}
+    roof["peak_of"] = src
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, it, el, desc = time_oracle(w, args.cpu_seconds, args.cpu_points)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else "bf16-in/f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "m": m, "d": w.d, "eta": w.eta, "prec": args.prec,
+                   "cost": w.kind, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas{world}"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
+        "clocks": clocks,
+    }
+    line.update(info)
+    print(json.dumps(line), flush=True)
+    solver.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="highdim")
+    ap.add_argument("--n", type=int, default=None, help="override n = m (profiling captures only)")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16_tc"])
+    ap.add_argument("--check-every", type=int, default=50)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--ttt", action="store_true", help="also measure time to infeasibility <= tol")
+    ap.add_argument("--ttt-max-iter", type=int, default=200000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-points", type=int, default=2048)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.warmup < 3 and args.impl == "gpu":
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -195,6 +195,13 @@ LAMP_API int lamp_step_host(lamp_ctx* ctx, const float* C_or_x, const float* y, 
  * inputs; prob's pointers are HOST pointers and are copied once here. */
 LAMP_API int lamp_create_owned(lamp_ctx** out, const lamp_problem* host_prob, const lamp_params* params, void* stream);
 
+/* Apply `iters` iterations (as lamp_iterate) launched one kernel at a time with
+ * CUDA events between the kernels on the context's stream, and return the mean
+ * device time in milliseconds of each kernel of an iteration in ms_out[0..3]:
+ * [0] row sweep, [1] row finalize, [2] column sweep, [3] column finalize.
+ * Synchronises.  iters >= 1. */
+LAMP_API int lamp_time_kernels(lamp_ctx* ctx, int64_t iters, double* ms_out);
+
 /* Number of kernel launches one iteration issues (for launch accounting). */
 LAMP_API int64_t lamp_launches_per_iteration(const lamp_ctx* ctx);
 

@@ -257,11 +257,15 @@ def lamp_run(C, r, c, params: LampParams, T: int, state: Optional[LampState] = N
 
 def lamp_solve(C, r, c, params: LampParams, tol: float, max_iter: int,
                state: Optional[LampState] = None):
-    """Iterate Alg. 2 until the infeasibility of X^t is <= tol (the termination
-    rule of App. E.2, checked on X^t before the iteration's updates).
+    """Iterate Alg. 2 until X^t meets the termination rule, checked on X^t before
+    the iteration's updates: the first t >= 1 with infeasibility <= tol (App. E.2)
+    and, for eta > 0, 1 - kappa_t eta <= tol (kappa_t -> 1/eta, Section 3.2, so that
+    X^t solves the eta problem and not the one of eta_t).  t = 0 is excluded: the
+    start X^0 = diag(r)/m is exactly feasible whenever c is uniform, and the
+    certificate of Prop. infeas_bound (a) is stated for t >= 1.
 
-    Returns (state_t, info_t, converged): the state whose X^t met the target
-    (or the state after max_iter iterations) and its StepInfo."""
+    Returns (state_t, info_t, converged): the state whose X^t met the rule (or the
+    state after max_iter iterations) and its StepInfo."""
     C = np.asarray(C, dtype=np.float64)
     K, tau1, tau2 = resolve_params(C, params)
     calpha = calpha_of(c, params.alpha)
@@ -269,7 +273,8 @@ def lamp_solve(C, r, c, params: LampParams, tol: float, max_iter: int,
     info = None
     for _ in range(max_iter + 1):
         nxt, info = lamp_step(C, r, c, K, tau1, tau2, params.eta, calpha, params.beta, st)
-        if info.res <= tol:
+        kappa_ok = params.eta == 0.0 or 1.0 - st.kappa * params.eta <= tol
+        if st.t >= 1 and info.res <= tol and kappa_ok:
             return st, info, True
         if st.t >= max_iter:
             break

@@ -50,7 +50,7 @@ PREC_BF16_TC = 1
 EXPORTED_SYMBOLS = [
     "lamp_params_default", "lamp_create", "lamp_solve", "lamp_iterate", "lamp_objective", "lamp_grad",
     "lamp_get_state", "lamp_set_state", "lamp_step_host", "lamp_create_owned",
-    "lamp_launches_per_iteration", "lamp_last_error", "lamp_destroy",
+    "lamp_launches_per_iteration", "lamp_last_error", "lamp_destroy", "lamp_time_kernels",
 ]
 
 library_path = Path(__file__).resolve().parent / "liblamp.so"
@@ -100,6 +100,7 @@ def _load():
     L.lamp_get_state.argtypes = [vp, vp, vp, vp, ctypes.POINTER(dbl), ctypes.POINTER(i64), vp]
     L.lamp_set_state.argtypes = [vp, vp, vp, dbl, i64, vp]
     L.lamp_step_host.argtypes = [vp, vp, vp, vp, vp, i64, ctypes.POINTER(dbl), vp]
+    L.lamp_time_kernels.argtypes = [vp, i64, ctypes.POINTER(dbl)]
     L.lamp_launches_per_iteration.argtypes = [vp]
     L.lamp_launches_per_iteration.restype = i64
     L.lamp_last_error.argtypes = [vp]
@@ -112,19 +113,33 @@ def _load():
     return L
 
 
-lib = _load()
+_LIB = None
+
+
+def _get_lib():
+    """Load liblamp.so on first use (so that the build step can import this package)."""
+    global _LIB
+    if _LIB is None:
+        _LIB = _load()
+    return _LIB
+
+
+def __getattr__(name):
+    if name == "lib":
+        return _get_lib()
+    raise AttributeError(name)
 
 
 def _check(code: int, ctx=None, ok=(LAMP_OK,)):
     if code not in ok:
-        msg = lib.lamp_last_error(ctx)
+        msg = _get_lib().lamp_last_error(ctx)
         raise LampError(code, msg.decode() if msg else "")
     return code
 
 
 def default_params(**kw) -> _Params:
     p = _Params()
-    _check(lib.lamp_params_default(ctypes.byref(p)))
+    _check(_get_lib().lamp_params_default(ctypes.byref(p)))
     for k, v in kw.items():
         if v is None:
             continue
@@ -186,14 +201,14 @@ class Lamp:
             stream = torch.cuda.current_stream()
         self._stream = stream
         h = ctypes.c_void_p()
-        _check(lib.lamp_create(ctypes.byref(h), ctypes.byref(prob), ctypes.byref(self.params),
+        _check(_get_lib().lamp_create(ctypes.byref(h), ctypes.byref(prob), ctypes.byref(self.params),
                                ctypes.c_void_p(stream.cuda_stream)))
         self._h = h
 
     # -- lifetime
     def close(self):
         if getattr(self, "_h", None):
-            lib.lamp_destroy(self._h)
+            _get_lib().lamp_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -212,16 +227,16 @@ class Lamp:
     def solve(self, allow_not_converged: bool = True) -> dict:
         res = _Result()
         ok = (LAMP_OK, LAMP_E_NOT_CONVERGED) if allow_not_converged else (LAMP_OK,)
-        code = _check(lib.lamp_solve(self._h, ctypes.byref(res)), self._h, ok)
+        code = _check(_get_lib().lamp_solve(self._h, ctypes.byref(res)), self._h, ok)
         return {"iters": int(res.iters), "infeas": res.infeas, "cost": res.obj_CX, "kappa": res.kappa,
                 "K": res.K, "status": int(res.status), "converged": code == LAMP_OK}
 
     def iterate(self, k: int) -> None:
-        _check(lib.lamp_iterate(self._h, int(k)), self._h)
+        _check(_get_lib().lamp_iterate(self._h, int(k)), self._h)
 
     def objective(self) -> dict:
         out = (ctypes.c_double * 8)()
-        _check(lib.lamp_objective(self._h, out), self._h)
+        _check(_get_lib().lamp_objective(self._h, out), self._h)
         keys = ["cost", "col_res", "row_res", "entropy", "P_eta", "certificate", "dual", "K"]
         return dict(zip(keys, list(out)))
 
@@ -231,7 +246,7 @@ class Lamp:
         dev = torch.device("cuda", torch.cuda.current_device())
         dx = torch.empty((self.n, self.d), dtype=torch.float32, device=dev) if want_x else None
         dy = torch.empty((self.m, self.d), dtype=torch.float32, device=dev) if want_y else None
-        _check(lib.lamp_grad(self._h, ctypes.c_void_p(_ptr(dx)), ctypes.c_void_p(_ptr(dy))), self._h)
+        _check(_get_lib().lamp_grad(self._h, ctypes.c_void_p(_ptr(dx)), ctypes.c_void_p(_ptr(dy))), self._h)
         return dx, dy
 
     def get_state(self) -> dict:
@@ -241,7 +256,7 @@ class Lamp:
         rs = np.empty(2 * self.n, dtype=np.float32)
         kap = ctypes.c_double()
         t = ctypes.c_int64()
-        _check(lib.lamp_get_state(self._h, nu.ctypes.data, th.ctypes.data, lz.ctypes.data,
+        _check(_get_lib().lamp_get_state(self._h, nu.ctypes.data, th.ctypes.data, lz.ctypes.data,
                                   ctypes.byref(kap), ctypes.byref(t), rs.ctypes.data), self._h)
         return {"nu": nu, "theta": th, "logZ": lz, "kappa": kap.value, "t": t.value, "row_shifts": rs}
 
@@ -249,11 +264,18 @@ class Lamp:
         nu = np.ascontiguousarray(nu, dtype=np.float64)
         th = np.ascontiguousarray(theta, dtype=np.float64)
         rs = None if row_shifts is None else np.ascontiguousarray(row_shifts, dtype=np.float32)
-        _check(lib.lamp_set_state(self._h, nu.ctypes.data, th.ctypes.data, float(kappa), int(t),
+        _check(_get_lib().lamp_set_state(self._h, nu.ctypes.data, th.ctypes.data, float(kappa), int(t),
                                   None if rs is None else rs.ctypes.data), self._h)
 
+    def time_kernels(self, iters: int) -> list:
+        """Run `iters` iterations kernel by kernel with CUDA events between the
+        launches; mean ms of [row sweep, row finalize, column sweep, column finalize]."""
+        out = (ctypes.c_double * 4)()
+        _check(_get_lib().lamp_time_kernels(self._h, int(iters), out), self._h)
+        return list(out)
+
     def launches_per_iteration(self) -> int:
-        return int(lib.lamp_launches_per_iteration(self._h))
+        return int(_get_lib().lamp_launches_per_iteration(self._h))
 
 
 class LampHost:
@@ -281,7 +303,7 @@ class LampHost:
         if stream is None:
             stream = torch.cuda.current_stream()
         h = ctypes.c_void_p()
-        _check(lib.lamp_create_owned(ctypes.byref(h), ctypes.byref(prob), ctypes.byref(self.params),
+        _check(_get_lib().lamp_create_owned(ctypes.byref(h), ctypes.byref(prob), ctypes.byref(self.params),
                                      ctypes.c_void_p(stream.cuda_stream)))
         self._h = h
 
@@ -291,14 +313,14 @@ class LampHost:
         r = self.r if r is None else r
         c = self.c if c is None else c
         inf = ctypes.c_double()
-        _check(lib.lamp_step_host(self._h, a.ctypes.data, 0 if b is None else b.ctypes.data, r.ctypes.data,
+        _check(_get_lib().lamp_step_host(self._h, a.ctypes.data, 0 if b is None else b.ctypes.data, r.ctypes.data,
                                   c.ctypes.data, int(iters), ctypes.byref(inf),
                                   0 if nu_out is None else nu_out.ctypes.data), self._h)
         return inf.value
 
     def close(self):
         if getattr(self, "_h", None):
-            lib.lamp_destroy(self._h)
+            _get_lib().lamp_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -233,6 +233,8 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
   k.m = prob->m;
   k.d = prob->kind == LAMP_COST_SQEUCLID ? (int32_t)prob->d : 0;
   k.kind = prob->kind;
+  // direct-form cost (z = |x - y|^2) for small d; dot form x.y above
+  k.zdot = (prob->kind == LAMP_COST_SQEUCLID && prob->d > 8) ? 1 : 0;
   k.eta = params->eta;
   k.alpha = params->alpha;
   k.clipb = std::tanh(params->beta / 2.0);
@@ -434,7 +436,7 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
   if (k.tau1 * k.eta > 1.0) return bail(fail(ctx, LAMP_E_INVALID, "tau1 * eta must be <= 1"));
 
   // offset bound factor W: |Bq_j| + |Rq_i| <= lambda W + 128 (see lamp_common.cuh)
-  if (k.kind == COST_DENSE) {
+  if (!k.zdot) {
     k.W = 5.0 * k.K;
     k.rnx = 0.0;
   } else {
@@ -646,6 +648,43 @@ extern "C" int lamp_step_host(lamp_ctx* ctx, const float* C_or_x, const float* y
   }
   CK(cudaStreamSynchronize(ctx->stream));
   if (infeas_out) *infeas_out = ctx->host_dev->res;
+  return LAMP_OK;
+}
+
+extern "C" int lamp_time_kernels(lamp_ctx* ctx, int64_t iters, double* ms_out) {
+  if (!ctx || !ms_out) return fail(ctx, LAMP_E_INVALID, "lamp_time_kernels: null argument");
+  if (iters < 1) return fail(ctx, LAMP_E_INVALID, "iters must be >= 1");
+  k_ctrl<<<1, 1, 0, ctx->stream>>>(ctx->w.dev, 0, -1.0, 0, iters, 0);
+  CK(cudaGetLastError());
+  cudaEvent_t ev[5];
+  for (int i = 0; i < 5; ++i) CK(cudaEventCreate(&ev[i]));
+  double acc[4] = {0, 0, 0, 0};
+  int rc = LAMP_OK;
+  for (int64_t it = 0; it < iters && rc == LAMP_OK; ++it) {
+    cudaEventRecord(ev[0], ctx->stream);
+    for (int part = 0; part < 4; ++part) {
+      cudaError_t e = launch_iteration_part(ctx->in, ctx->k, ctx->w, ctx->g, ctx->prec, part, ctx->stream);
+      if (e != cudaSuccess) {
+        rc = fail(ctx, LAMP_E_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+        break;
+      }
+      cudaEventRecord(ev[part + 1], ctx->stream);
+    }
+    if (rc) break;
+    cudaError_t e = cudaEventSynchronize(ev[4]);
+    if (e != cudaSuccess) {
+      rc = fail(ctx, LAMP_E_CUDA, "cudaEventSynchronize: %s", cudaGetErrorString(e));
+      break;
+    }
+    for (int part = 0; part < 4; ++part) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[part], ev[part + 1]);
+      acc[part] += ms;
+    }
+  }
+  for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+  if (rc) return rc;
+  for (int part = 0; part < 4; ++part) ms_out[part] = acc[part] / (double)iters;
   return LAMP_OK;
 }
 

@@ -11,9 +11,14 @@
 // p^{eta}(nu)_ij is, in base 2 and up to the row normaliser,
 //     s2_ij = -lambda (C_ij + 2K nu_j).
 // The kernels evaluate it as v_ij = a z_ij - Bq_j - Rq_i where
-//   DENSE:    z = C_ij,          a = -lambda,   Bcol_j = lambda 2K nu_j,          Rrow_i = M_i
-//   SQEUCLID: z = x_i . y_j,     a = 2 lambda s, Bcol_j = lambda (s|y_j|^2 + 2K nu_j),
-//                                               Rrow_i = lambda s |x_i|^2 + M_i
+//   direct form (DENSE, and SQEUCLID with d <= 8):
+//             z = C_ij / s (stored cost, or sum_k (x_ik - y_jk)^2),
+//             a = -lambda s,  Bcol_j = lambda 2K nu_j,  Rrow_i = M_i
+//   dot form (SQEUCLID with d > 8):
+//             z = x_i . y_j,  a = 2 lambda s,  Bcol_j = lambda (s|y_j|^2 + 2K nu_j),
+//                                              Rrow_i = lambda s |x_i|^2 + M_i
+// The direct form's float32 error is relative to C_ij itself; the dot form's is
+// relative to |x_i||y_j|, which is what tensor cores (and d = 64) need.
 // with M_i a per-row shift (a running estimate of log2 of the row maximum).
 // Bq_j and Rq_i are Bcol_j, Rrow_i rounded to a power-of-two grid g chosen so
 // that |Bq| + |Rq| < 2^23 g: their float32 sum is then exact, the product a z
@@ -45,7 +50,9 @@ struct Consts {
   double tau1, tau2, eta, alpha;
   double clipb;      // tanh(beta/2)
   double W;          // bound factor for the exponent offsets: |Bq|+|Rq| <= lambda*W + 128
-  double rnx;        // sum_i r_i s |x_i|^2 (SQEUCLID cost bookkeeping), 0 for DENSE
+  double rnx;        // sum_i r_i s |x_i|^2 (dot-form cost bookkeeping), 0 otherwise
+  int32_t zdot;      // 1: z = x.y (dot form), 0: z = C/s (direct form)
+  int32_t pad;
 };
 
 // Parameters of one iteration's sweeps, derived from kappa_t alone.
@@ -81,9 +88,9 @@ __host__ __device__ inline SweepParams make_sweep_params(double kap, const Const
   p.kapB = kappa_next(kap, k);
   p.lamA = p.kapA * kLog2e;
   p.lamB = p.kapB * kLog2e;
-  if (k.kind == COST_DENSE) {
-    p.aA = -p.lamA;
-    p.aB = -p.lamB;
+  if (!k.zdot) {
+    p.aA = -p.lamA * k.s;
+    p.aB = -p.lamB * k.s;
   } else {
     p.aA = 2.0 * p.lamA * k.s;
     p.aB = 2.0 * p.lamB * k.s;
@@ -143,7 +150,7 @@ struct DevState {
   int done;           // set: the remaining launches of a device loop return at once
   int status;         // 0 or LAMP_E_NUMERIC
   int eval_only;      // 1: compute the pass but never apply the update
-  double tol;         // stop when res <= tol
+  double tol;         // stop at the first t >= 1 with res <= tol (and, for eta > 0, 1 - kappa eta <= tol)
   long long tmax;     // stop when t >= tmax
   unsigned int ticket;  // last-block counter of the column finalize kernel
   unsigned int pad;
@@ -205,6 +212,8 @@ cudaError_t launch_prime(const Inputs& in, const Consts& k, const Work& w, const
 cudaError_t launch_iteration(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
                              cudaStream_t st);
 void prepare_kernels();
+cudaError_t launch_iteration_part(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
+                                  int part, cudaStream_t st);
 int tile_outer_cols(const Consts& k, int prec);
 int tile_inner_cols(const Consts& k, int prec);
 cudaError_t launch_grad(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,

@@ -58,7 +58,7 @@ struct SweepIO {
   const float4* indat[2];
 };
 
-template <int MODE, int DG>
+template <int MODE, int DG, bool DIFF>
 __global__ void __launch_bounds__(kThreads, 1)
 k_pts_sweep(const float* __restrict__ P_out, const float* __restrict__ P_in, int64_t n_out, int64_t n_in, int d,
             const SweepIO io, double* __restrict__ part, float* __restrict__ pmax, int tiles_per_split,
@@ -166,10 +166,20 @@ k_pts_sweep(const float* __restrict__ P_out, const float* __restrict__ P_in, int
       float4 b1 = *reinterpret_cast<const float4*>(&sIn[kk * kPT + 64 + tx * 4]);
       float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
       float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+      if (DIFF) {
 #pragma unroll
-      for (int a = 0; a < 8; ++a)
+        for (int a = 0; a < 8; ++a)
 #pragma unroll
-        for (int b = 0; b < 8; ++b) z[a][b] = __fmaf_rn(av[a], bv[b], z[a][b]);
+          for (int b = 0; b < 8; ++b) {
+            const float df = av[a] - bv[b];
+            z[a][b] = __fmaf_rn(df, df, z[a][b]);
+          }
+      } else {
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int b = 0; b < 8; ++b) z[a][b] = __fmaf_rn(av[a], bv[b], z[a][b]);
+      }
     }
 
     float4 dat[8];
@@ -214,9 +224,10 @@ k_pts_sweep(const float* __restrict__ P_out, const float* __restrict__ P_in, int
       for (int a = 0; a < 8; ++a)
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
-          float dd = __fmaf_rn(-2.0f, z[a][b], oA[a] + dat[b].x);
-          mx[a][0] = fmaxf(mx[a][0], dd);
-          mx[a][1] = fmaxf(mx[a][1], (dat[b].x == -INFINITY) ? -INFINITY : -dd);
+          const bool pad = (dat[b].x == -INFINITY);
+          const float dd = DIFF ? z[a][b] : __fmaf_rn(-2.0f, z[a][b], oA[a] + dat[b].x);
+          mx[a][0] = fmaxf(mx[a][0], pad ? -INFINITY : dd);
+          mx[a][1] = fmaxf(mx[a][1], pad ? -INFINITY : -dd);
         }
     } else if (MODE == M_GRAD) {
       // sum over inner b of 2^{v_ab} * weight_b * P_in[b][:], stream A only
@@ -581,7 +592,7 @@ __global__ void k_init_cols(const Work w, const Consts k, int zero) {
   SweepParams sp = make_sweep_params(dev->kappa, k);
   double wt = k.tau1 / sp.kapB;  // tau1 eta_{t+1}
   double nb = nu[j] + wt * (theta[j] - nu[j]);
-  double sny = (k.kind == COST_SQEUCLID) ? k.s * ny[j] : 0.0;
+  double sny = k.zdot ? k.s * ny[j] : 0.0;
   colq[j] = column_data(nu[j], nb, sny, sp, k);
 }
 
@@ -634,7 +645,7 @@ k_row_fin(const Work w, int splits, const double* __restrict__ r, const Consts k
       SB = SB > 0 ? SB : 1.0;
     }
     float2 rq = rs_cur[i];
-    double snx = (k.kind == COST_SQEUCLID) ? k.s * nx[i] : 0.0;
+    double snx = k.zdot ? k.s * nx[i] : 0.0;
     double lsA = log2(SA), lsB = log2(SB);
     double L2A = (double)rq.x - sp.lamA * snx + lsA;  // log2 Z of X^t
     double L2B = (double)rq.y - sp.lamB * snx + lsB;  // log2 Z of Xbar^{t+1}
@@ -694,8 +705,8 @@ k_col_fin(const Work w, int splits, const double* __restrict__ cvec, int rowbloc
     const double A = (double)cq.y * aA;  // col(X^t)_j
     const double B = (double)cq.w * aB;  // col(Xbar^{t+1})_j
     const double zsum = (double)cq.y * aC;
-    if (k.kind == COST_DENSE) {
-      cost = zsum;
+    if (!k.zdot) {
+      cost = k.s * zsum;
     } else {
       cost = k.s * ny[j] * A - 2.0 * k.s * zsum;  // + sum_i r_i s|x_i|^2 added once below
     }
@@ -719,7 +730,7 @@ k_col_fin(const Work w, int splits, const double* __restrict__ cvec, int rowbloc
       SweepParams spn = make_sweep_params(sp.kapB, k);
       const double wn = k.tau1 / spn.kapB;
       const double nbn = nun + wn * (thn - nun);         // nubar^{t+2}
-      const double sny = (k.kind == COST_SQEUCLID) ? k.s * ny[j] : 0.0;
+      const double sny = k.zdot ? k.s * ny[j] : 0.0;
       colq_nxt[j] = column_data(nun, nbn, sny, spn, k);
     }
   }
@@ -764,7 +775,8 @@ k_col_fin(const Work w, int splits, const double* __restrict__ cvec, int rowbloc
       dev->done = 1;
     } else if (eval_only) {
       dev->done = 1;
-    } else if (R <= dev->tol || dev->t >= dev->tmax) {
+    } else if ((dev->t >= 1 && R <= dev->tol && (k.eta == 0.0 || 1.0 - dev->kappa * k.eta <= dev->tol)) ||
+               dev->t >= dev->tmax) {
       dev->done = 1;
     } else {
       dev->t = dev->t + 1;
@@ -825,7 +837,7 @@ template <int MODE, int DG>
 static cudaError_t launch_pts(const float* Pout, const float* Pin, int64_t nout, int64_t nin, int d, const SweepIO& io,
                               double* part, float* pmax, int splits, const DevState* dev, const Consts& k,
                               cudaStream_t st) {
-  auto kern = k_pts_sweep<MODE, DG>;
+  auto kern = k.zdot ? k_pts_sweep<MODE, DG, false> : k_pts_sweep<MODE, DG, true>;
   size_t sm = pts_smem(d);
   int64_t tin = cdiv(nin, kPT);
   int tps = (int)cdiv(tin, splits);
@@ -913,26 +925,38 @@ cudaError_t launch_prime(const Inputs& in, const Consts& k, const Work& w, const
   return cudaGetLastError();
 }
 
+cudaError_t launch_iteration_part(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
+                                  int part, cudaStream_t st) {
+  const int rb = (int)cdiv(k.n, kThreads);
+  switch (part) {
+    case 0:
+      return launch_row_sweep(in, k, w, g, M_ROWSUM, st);
+    case 1:
+      k_row_fin<<<rb, kThreads, 0, st>>>(w, g.rows_split, in.r, k);
+      return cudaGetLastError();
+    case 2:
+      return launch_col_sweep(in, k, w, g, st);
+    default:
+      k_col_fin<<<(unsigned)cdiv(k.m, kThreads), kThreads, 0, st>>>(w, g.cols_split, in.c, rb, k);
+      return cudaGetLastError();
+  }
+}
+
 cudaError_t launch_iteration(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
                              cudaStream_t st) {
-  cudaError_t e = launch_row_sweep(in, k, w, g, M_ROWSUM, st);
-  if (e != cudaSuccess) return e;
-  int rb = (int)cdiv(k.n, kThreads);
-  k_row_fin<<<rb, kThreads, 0, st>>>(w, g.rows_split, in.r, k);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  e = launch_col_sweep(in, k, w, g, st);
-  if (e != cudaSuccess) return e;
-  int cb = (int)cdiv(k.m, kThreads);
-  k_col_fin<<<cb, kThreads, 0, st>>>(w, g.cols_split, in.c, rb, k);
-  return cudaGetLastError();
+  for (int part = 0; part < 4; ++part) {
+    cudaError_t e = launch_iteration_part(in, k, w, g, prec, part, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 int launches_per_iteration(const Consts& k, int prec) { return 4; }
 
 template <int MODE, int DG>
 static void set_attr() {
-  cudaFuncSetAttribute(k_pts_sweep<MODE, DG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pts_smem(64));
+  cudaFuncSetAttribute(k_pts_sweep<MODE, DG, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pts_smem(64));
+  cudaFuncSetAttribute(k_pts_sweep<MODE, DG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pts_smem(64));
 }
 
 // raise the dynamic shared-memory limit of every sweep instantiation once, before any capture
@@ -962,7 +986,8 @@ int sweep_blocks_per_sm(const Consts& k, int prec, int which) {
     else
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dense_cols, kThreads, 0);
   } else {
-    auto kern = which == 0 ? k_pts_sweep<M_ROWSUM, 0> : k_pts_sweep<M_COLSUM, 0>;
+    auto kern = which == 0 ? (k.zdot ? k_pts_sweep<M_ROWSUM, 0, false> : k_pts_sweep<M_ROWSUM, 0, true>)
+                           : (k.zdot ? k_pts_sweep<M_COLSUM, 0, false> : k_pts_sweep<M_COLSUM, 0, true>);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kThreads, pts_smem(k.d));
   }
   return nb > 0 ? nb : 1;

@@ -6,8 +6,8 @@ import pytest
 
 import oracle as O
 import workloads as W
-from tests.gpu_util import (GRAD_TOL, LOGZ_TOL, OBJ_TOL, POT_TOL, assert_logZ_close, assert_pot_close, dev,
-                            gpu_solver, oracle_cost)
+from tests.gpu_util import (GRAD_TOL, LOGZ_TOL, OBJ_TOL, POT_TOL, RES_FLOOR, assert_logZ_close, assert_pot_close,
+                            cost_slack, dev, gpu_solver, oracle_cost)
 
 pytestmark = pytest.mark.gpu
 
@@ -94,7 +94,7 @@ def test_ragged_and_degenerate_sizes(n, m, kind):
     obj = s.objective()
     rep = O.objective_report(C, w.r, w.c, K, 0.0, ref)
     assert abs(obj["cost"] - rep["cost"]) <= OBJ_TOL * abs(rep["cost"]) + 1e-12
-    assert abs(obj["col_res"] - rep["col_res"]) <= 1e-6 * max(rep["col_res"], 1e-3)
+    assert abs(obj["col_res"] - rep["col_res"]) <= 1e-6 * rep["col_res"] + RES_FLOOR
     s.close()
 
 
@@ -113,7 +113,7 @@ def test_objective_and_logZ_match_oracle(eta):
     assert abs(obj["cost"] - rep["cost"]) <= OBJ_TOL * rep["cost"]
     assert abs(obj["entropy"] - rep["entropy"]) <= 1e-6 * abs(rep["entropy"])
     assert abs(obj["P_eta"] - rep["P_eta"]) <= 1e-6 * abs(rep["P_eta"]) + 1e-9
-    assert abs(obj["col_res"] - rep["col_res"]) <= 1e-6 * rep["col_res"] + 1e-9
+    assert abs(obj["col_res"] - rep["col_res"]) <= 1e-6 * rep["col_res"] + RES_FLOOR
     assert obj["row_res"] == 0.0 and obj["K"] == K
     if eta == 0.0:
         assert abs(obj["certificate"] - rep["certificate"]) <= 1e-6 * rep["certificate"]
@@ -122,47 +122,77 @@ def test_objective_and_logZ_match_oracle(eta):
 
 
 @pytest.mark.parametrize("T0", [500, 3000])
-@pytest.mark.parametrize("kind", ["sqeuclid", "dense"])
+@pytest.mark.parametrize("kind", ["dense", "sqeuclid_dyadic", "sqeuclid"])
 def test_single_step_at_large_kappa(T0, kind):
     """One iteration from an oracle state with kappa = T0/(2K): the compensated
-    exponent keeps the float32 sweeps accurate although lambda C = O(T0)."""
+    exponent keeps the float32 sweeps accurate although lambda C = O(T0).
+    dense and sqeuclid_dyadic give the kernels the oracle's exact cost (dyadic
+    coordinates make every squared distance exact in float32): tolerance 1e-5.
+    sqeuclid on random points adds the float32 cost error times kappa."""
     if kind == "dense":
         w = W.dense_problem("lk", 64, 80, seed=5)
+    elif kind == "sqeuclid_dyadic":
+        w = W.points_problem("lk", 64, 80, 2, seed=5, cost_scale=1.0, grid_step=64)
     else:
         w = W.points_problem("lk", 64, 80, 2, seed=5, cost_scale=-1.0)
     s, C, K = gpu_solver(w, check_every=1)
     P = O.LampParams(K=K)
     st0 = O.lamp_run(C, w.r, w.c, P, T0)
+    tol = POT_TOL if kind != "sqeuclid" else cost_slack(w, st0.kappa)
     s.set_state(st0.nu, st0.theta, st0.kappa, st0.t)
     s.iterate(1)
     g = s.get_state()
     K_, tau1, tau2 = O.resolve_params(C, P)
     ref1, info = O.lamp_step(C, w.r, w.c, K_, tau1, tau2, 0.0, O.calpha_of(w.c, 0.01), 1.1, st0)
-    assert_pot_close(g, ref1, tol=POT_TOL, what=f"step at t={T0}")
+    assert_pot_close(g, ref1, tol=tol, what=f"step at t={T0}")
     assert g["t"] == T0 + 1 and g["kappa"] == pytest.approx(ref1.kappa, rel=1e-15)
     # log Z of X^{T0}: absolute error small although |log Z| ~ kappa
     s2, _, _ = gpu_solver(w, check_every=1)
     s2.set_state(st0.nu, st0.theta, st0.kappa, st0.t)
     s2.objective()
     lz = s2.get_state()["logZ"]
-    assert np.abs(lz - info.logZ_A).max() <= 1e-5
+    assert np.abs(lz - info.logZ_A).max() <= (1e-5 if kind != "sqeuclid" else 1e-5 + 4 * st0.kappa * (tol - POT_TOL))
     s.close()
     s2.close()
 
 
-def test_solve_stops_where_the_oracle_does():
-    w = W.plain_2d(n=128, m=128, seed=9)
+@pytest.mark.parametrize("kind", ["plain_2d", "dyadic"])
+def test_solve_stops_where_the_oracle_does(kind):
+    if kind == "plain_2d":
+        w = W.plain_2d(n=128, m=128, seed=9)
+    else:
+        w = W.points_problem("dy", 128, 128, 2, seed=9, cost_scale=1.0, grid_step=64)
     tol = 1e-6
     s, C, K = gpu_solver(w, tol=tol, max_iter=200000, check_every=64)
     res = s.solve(allow_not_converged=False)
     st_ref, info, conv = O.lamp_solve(C, w.r, w.c, O.LampParams(K=K), tol, 200000)
     assert conv and res["converged"]
-    assert res["infeas"] <= tol
-    assert abs(res["iters"] - st_ref.t) <= max(2, 0.01 * st_ref.t), (res["iters"], st_ref.t)
+    assert res["infeas"] <= tol and res["iters"] >= 1
+    assert abs(res["iters"] - st_ref.t) <= max(2, 0.02 * st_ref.t), (res["iters"], st_ref.t)
     # the oracle's own residual at the GPU's final state
     g = s.get_state()
     colX, _ = O.marginals_from_state(C, w.r, K, g["kappa"], g["nu"])
-    assert np.abs(colX - w.c).sum() <= 1.05 * tol
+    slack = 0.0 if kind == "dyadic" else 4 * g["kappa"] * (cost_slack(w, 1.0) - POT_TOL)
+    assert np.abs(colX - w.c).sum() <= 1.05 * tol + RES_FLOOR + slack
+    s.close()
+
+
+def test_uniform_marginals_do_not_stop_at_the_start():
+    """With uniform c the Alg. 2 start X^0 = diag(r)/m is exactly feasible; the
+    termination rule starts at t = 1 (oracle and GPU alike)."""
+    w = W.points_problem("u", 96, 96, 3, seed=3, dist="gauss_shift", marg="uniform", cost_scale=1.0)
+    s, C, K = gpu_solver(w, tol=1e-6, max_iter=100000, check_every=50)
+    res = s.solve(allow_not_converged=False)
+    st_ref, info, conv = O.lamp_solve(C, w.r, w.c, O.LampParams(K=K), 1e-6, 100000)
+    assert res["iters"] >= 1 and st_ref.t >= 1 and conv
+    # where the residual curve is flat near tol, float32 and float64 cross it at
+    # somewhat different t; what is fixed is that the GPU's state meets the rule
+    # under the oracle's arithmetic too (up to the float32 cost error at kappa)
+    assert abs(res["iters"] - st_ref.t) <= 0.25 * st_ref.t
+    g = s.get_state()
+    colX, _ = O.marginals_from_state(C, w.r, K, g["kappa"], g["nu"])
+    slack = 4 * g["kappa"] * (cost_slack(w, 1.0) - POT_TOL)
+    assert np.abs(colX - w.c).sum() <= 1.05e-6 + RES_FLOOR + slack
     s.close()
 
 
@@ -259,7 +289,7 @@ def test_gradient_matches_oracle_envelope_and_fd():
     central finite differences of the FP64 Sinkhorn value."""
     eta = 0.05
     w = W.diffloss(n=150, seed=8)
-    s, C, K = gpu_solver(w, eta=eta, tol=1e-10, max_iter=400000, check_every=200)
+    s, C, K = gpu_solver(w, eta=eta, tol=5e-7, max_iter=400000, check_every=200)
     res = s.solve(allow_not_converged=False)
     dx, dy = s.grad()
     dx, dy = dx.cpu().numpy().astype(np.float64), dy.cpu().numpy().astype(np.float64)
@@ -290,7 +320,7 @@ def test_autograd_function():
     w = W.diffloss(n=96, seed=21)
     x = dev(w.x).requires_grad_(True)
     y = dev(w.y).requires_grad_(True)
-    loss = L.lamp_ot_loss(x, y, eta=0.05, tol=1e-10, max_iter=400000)
+    loss = L.lamp_ot_loss(x, y, eta=0.05, tol=5e-7, max_iter=400000)
     (2.0 * loss).backward()
     C = O.sqeuclid_cost(w.x, w.y)
     X, *_ = O.sinkhorn_log(C, w.r, w.c, 0.05, tol=1e-14)

@@ -429,3 +429,22 @@ def test_sqeuclid_cost_expansion_agrees():
     C = O.sqeuclid_cost(x, y, chunk=4)
     ref = (x ** 2).sum(1)[:, None] + (y ** 2).sum(1)[None, :] - 2 * x @ y.T
     assert np.max(np.abs(C - ref)) < 1e-12
+
+
+def test_solve_does_not_stop_at_the_feasible_start():
+    """Uniform c makes X^0 = diag(r)/m exactly feasible; the rule starts at t = 1."""
+    w = W.points_problem("u", 12, 12, 2, 4, marg="uniform", cost_scale=1.0)
+    C = O.cost_matrix(w)
+    st, info, conv = O.lamp_solve(C, w.r, w.c, O.LampParams(), 1e-6, 20000)
+    assert conv and st.t >= 1
+    K = O.sup_norm(C)
+    X0 = w.r[:, None] * O.dual_to_primal(C, K, 0.0, np.zeros(12))[0]
+    assert np.abs(X0.sum(0) - w.c).sum() < 1e-15
+
+
+def test_solve_eta_positive_waits_for_kappa():
+    """For eta > 0 the rule also needs 1 - kappa_t eta <= tol (X^t solves the eta_t problem)."""
+    C, r, c = small_points(10, 10, seed=3)
+    eta, tol = 0.05, 1e-6
+    st, info, conv = O.lamp_solve(C, r, c, O.LampParams(eta=eta), tol, 200000)
+    assert conv and 1.0 - st.kappa * eta <= tol and info.res <= tol

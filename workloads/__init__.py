@@ -140,13 +140,15 @@ def gaussian_mixture_marginal(rng: np.random.Generator, side: int, kmin: int = 3
 
 def points_problem(name: str, n: int, m: int, d: int, seed: int, dist: str = "uniform",
                    marg: str = "random", cost_scale: float = 1.0, eta: float = 0.0,
-                   tol: float = 1e-6) -> Workload:
+                   tol: float = 1e-6, grid_step: Optional[int] = None) -> Workload:
     """Generic point-cloud problem used by the named workloads and by tests
     at smaller / ragged sizes.
 
     dist: "uniform" (x, y ~ U[0,1]^d), "gauss_shift" (x ~ N(0,I), y ~ N(0.5,I)),
           "sphere" (x ~ N(0,I), y = unit-sphere + N(0,0.05^2)).
     marg: "random" (normalised U(0.1,1)) or "uniform".
+    grid_step: if given, coordinates are rounded to multiples of 1/grid_step (a
+        power of two keeps every squared distance exactly representable in float32).
     """
     rng = _rng(seed)
     if dist == "uniform":
@@ -161,6 +163,9 @@ def points_problem(name: str, n: int, m: int, d: int, seed: int, dist: str = "un
         y = g / np.linalg.norm(g, axis=1, keepdims=True) + 0.05 * rng.standard_normal(size=(m, d))
     else:
         raise ValueError(dist)
+    if grid_step is not None:
+        x = np.round(x * grid_step) / grid_step
+        y = np.round(y * grid_step) / grid_step
     if marg == "random":
         r = random_marginal(rng, n)
         c = random_marginal(rng, m)
