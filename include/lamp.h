@@ -207,6 +207,32 @@ LAMP_API int64_t lamp_launches_per_iteration(const lamp_ctx* ctx);
 
 LAMP_API const char* lamp_last_error(const lamp_ctx* ctx);
 
+/* Allocation-free evaluation of one coupling's marginals.  The paper has no
+ * counterpart: it exists for callers that may not call cudaMalloc where they
+ * run, such as plugins whose host framework owns every byte of device memory
+ * through its own pool, or latency-bound loops that cannot afford the device
+ * synchronisation cudaMalloc/cudaFree can cause.  No context is created.
+ *
+ * For X = diag(r) p^{1/kappa}(nu) it writes log Z (n doubles, natural log) to
+ * logZ_out, col(X) (m doubles) to col_out and <C, X> (one double, NaN if a row
+ * sum left the representable range; may be NULL) to cost_out.  prob holds
+ * DEVICE pointers (DENSE, or SQEUCLID with d <= 8 and an explicit cost_scale > 0);
+ * K > 0 is the ||C||_inf to use; kappa >= 0; nu: m doubles on the device.
+ * Work is enqueued on `stream`; the call returns without synchronising.
+ *
+ * Scratch comes from a 16 MiB array compiled into the library (each GPU that
+ * loads the library keeps it until the process exits).  Requests whose
+ * workspace does not fit (about 136 n + 168 m bytes) return LAMP_E_INVALID.
+ * The first call on a device looks up the array's device address; make it
+ * before starting any stream capture.  All calls on a device share the array:
+ * calls whose GPU work overlaps (other streams, other threads) race and
+ * corrupt each other, so issue them one after another on one stream.  The
+ * array keeps the previous call's contents; the call clears what must start
+ * at zero.  Errors: LAMP_E_INVALID, LAMP_E_UNSUPPORTED (d > 8), LAMP_E_CUDA;
+ * the message is in lamp_last_error(NULL). */
+LAMP_API int lamp_marginals_noalloc(const lamp_problem* prob, double K, double kappa, const double* nu,
+                                    double* logZ_out, double* col_out, double* cost_out, void* stream);
+
 /* Release everything the context owns (NULL is a no-op). */
 LAMP_API void lamp_destroy(lamp_ctx* ctx);
 

@@ -51,6 +51,7 @@ EXPORTED_SYMBOLS = [
     "lamp_params_default", "lamp_create", "lamp_solve", "lamp_iterate", "lamp_objective", "lamp_grad",
     "lamp_get_state", "lamp_set_state", "lamp_step_host", "lamp_create_owned",
     "lamp_launches_per_iteration", "lamp_last_error", "lamp_destroy", "lamp_time_kernels",
+    "lamp_marginals_noalloc",
 ]
 
 library_path = Path(__file__).resolve().parent / "liblamp.so"

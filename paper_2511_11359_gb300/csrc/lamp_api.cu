@@ -44,6 +44,8 @@ struct lamp_ctx {
 
 static thread_local std::string g_err;
 
+void lamp::set_last_error_null(const char* msg) { g_err = msg ? msg : ""; }
+
 static int fail(lamp_ctx* ctx, int code, const char* fmt, ...) {
   char buf[512];
   va_list ap;

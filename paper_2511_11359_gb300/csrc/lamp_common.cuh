@@ -219,6 +219,8 @@ int tile_inner_cols(const Consts& k, int prec);
 cudaError_t launch_grad(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
                         float* dx, float* dy, cudaStream_t st);
 int launches_per_iteration(const Consts& k, int prec);
+// record a message for lamp_last_error(NULL) (errors raised without a context)
+void set_last_error_null(const char* msg);
 int sweep_blocks_per_sm(const Consts& k, int prec, int which);
 int tile_outer(const Consts& k, int prec);
 int tile_inner(const Consts& k, int prec);
