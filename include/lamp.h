@@ -187,7 +187,8 @@ LAMP_API int lamp_set_state(lamp_ctx* ctx, const double* nu, const double* theta
  * (DENSE) and r, c from HOST memory into device buffers the context owns, run
  * `iters` iterations, and copy the infeasibility of the last evaluated X^t and
  * nu (m doubles, may be NULL) back to host memory.  The context must have been
- * created with lamp_create_owned.  Synchronises. */
+ * created with lamp_create_owned, and the uploaded data must describe the same
+ * problem (K and the squared norms are not recomputed).  Synchronises. */
 LAMP_API int lamp_step_host(lamp_ctx* ctx, const float* C_or_x, const float* y, const double* r, const double* c,
                    int64_t iters, double* infeas_out, double* nu_out);
 

@@ -39,6 +39,14 @@ struct lamp_ctx {
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   int64_t glen[2] = {0, 0};
   DevState* host_dev = nullptr;  // pinned mirror for polling
+  // LAMP_PREC_BF16_TC: bf16 copies (zero padded to 128-row multiples x 64 coordinates),
+  // float32 copies of the rounded points, and their TMA descriptors
+  void* xb = nullptr;
+  void* yb = nullptr;
+  float* xr = nullptr;
+  float* yr = nullptr;
+  alignas(64) unsigned char map_x[128];
+  alignas(64) unsigned char map_y[128];
   std::string err;
 };
 
@@ -126,8 +134,8 @@ static int validate(const lamp_problem* pr, const lamp_params* pa, bool device_p
     return fail(nullptr, LAMP_E_INVALID, "check_every must be in [1, 100000]");
   if (pa->prec != LAMP_PREC_FP32 && pa->prec != LAMP_PREC_BF16_TC)
     return fail(nullptr, LAMP_E_INVALID, "unknown precision %d", pa->prec);
-  if (pa->prec == LAMP_PREC_BF16_TC)
-    return fail(nullptr, LAMP_E_UNSUPPORTED, "LAMP_PREC_BF16_TC is not available in this build");
+  if (pa->prec == LAMP_PREC_BF16_TC && pr->kind != LAMP_COST_SQEUCLID)
+    return fail(nullptr, LAMP_E_INVALID, "LAMP_PREC_BF16_TC applies to LAMP_COST_SQEUCLID only");
   if (!(pa->K >= 0.0) || !std::isfinite(pa->K)) return fail(nullptr, LAMP_E_INVALID, "K must be >= 0");
   if (pa->tau1 > 0.0 && pa->tau1 * pa->eta > 1.0) return fail(nullptr, LAMP_E_INVALID, "tau1 * eta must be <= 1");
   (void)device_ptrs;
@@ -230,13 +238,21 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
     }
   }
   prepare_kernels();
+  if (params->prec == LAMP_PREC_BF16_TC) {
+    cudaError_t e = tc_prepare();
+    if (e != cudaSuccess) {
+      fail(nullptr, LAMP_E_CUDA, "tcgen05 kernel setup: %s", cudaGetErrorString(e));
+      delete ctx;
+      return LAMP_E_CUDA;
+    }
+  }
   Consts& k = ctx->k;
   k.n = prob->n;
   k.m = prob->m;
   k.d = prob->kind == LAMP_COST_SQEUCLID ? (int32_t)prob->d : 0;
   k.kind = prob->kind;
   // direct-form cost (z = |x - y|^2) for small d; dot form x.y above
-  k.zdot = (prob->kind == LAMP_COST_SQEUCLID && prob->d > 8) ? 1 : 0;
+  k.zdot = (prob->kind == LAMP_COST_SQEUCLID && (prob->d > 8 || params->prec == LAMP_PREC_BF16_TC)) ? 1 : 0;
   k.eta = params->eta;
   k.alpha = params->alpha;
   k.clipb = std::tanh(params->beta / 2.0);
@@ -296,8 +312,9 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
     g.sms = prop.multiProcessorCount;
   }
   {
-    int bpr = sweep_blocks_per_sm(k, ctx->prec, 0);
-    int bpc = sweep_blocks_per_sm(k, ctx->prec, 1);
+    const bool tcp = ctx->prec == LAMP_PREC_BF16_TC;
+    int bpr = tcp ? tc_blocks_per_sm(0) : sweep_blocks_per_sm(k, ctx->prec, 0);
+    int bpc = tcp ? tc_blocks_per_sm(1) : sweep_blocks_per_sm(k, ctx->prec, 1);
     int64_t to = (k.n + tile_outer(k, ctx->prec) - 1) / tile_outer(k, ctx->prec);
     int64_t ti = (k.m + tile_inner(k, ctx->prec) - 1) / tile_inner(k, ctx->prec);
     int64_t tco = (k.m + tile_outer_cols(k, ctx->prec) - 1) / tile_outer_cols(k, ctx->prec);
@@ -315,13 +332,15 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
   ctx->rowblocks = (int)((k.n + 255) / 256);
   int colblocks = (int)((k.m + 255) / 256);
   size_t gradd = k.kind == LAMP_COST_SQEUCLID ? (size_t)std::min<int64_t>(std::max<int64_t>(k.d, 2), 8) : 2;
+  // column / row data are padded to 128-entry multiples (padding entries contribute nothing)
+  const size_t m_pad = (size_t)tc_pad(k.m), n_pad = (size_t)tc_pad(k.n);
   for (int b = 0; b < 2; ++b) {
     if ((rc = dalloc(ctx, &w.nu[b], m))) return bail(rc);
     if ((rc = dalloc(ctx, &w.theta[b], m))) return bail(rc);
-    if ((rc = dalloc(ctx, &w.colq[b], m))) return bail(rc);
+    if ((rc = dalloc(ctx, &w.colq[b], m_pad))) return bail(rc);
     if ((rc = dalloc(ctx, &w.rowshift[b], n))) return bail(rc);
   }
-  if ((rc = dalloc(ctx, &w.g2row, n))) return bail(rc);
+  if ((rc = dalloc(ctx, &w.g2row, n_pad))) return bail(rc);
   if ((rc = dalloc(ctx, &w.rowpart, (size_t)g.rows_split * std::max<size_t>(2, gradd) * n))) return bail(rc);
   if ((rc = dalloc(ctx, &w.colpart, (size_t)g.cols_split * std::max<size_t>(3, gradd) * m))) return bail(rc);
   if ((rc = dalloc(ctx, &w.logZ, n))) return bail(rc);
@@ -342,6 +361,9 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
   {
     cudaError_t e = cudaMemcpyAsync(w.dev, ctx->host_dev, sizeof(DevState), cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return bail(fail(ctx, LAMP_E_CUDA, "init copy: %s", cudaGetErrorString(e)));
+    tc_fill_pads(w.colq[0], k.m, (int64_t)m_pad, ctx->stream);
+    tc_fill_pads(w.colq[1], k.m, (int64_t)m_pad, ctx->stream);
+    tc_fill_pads(w.g2row, k.n, (int64_t)n_pad, ctx->stream);
     cudaMemsetAsync(w.nu[0], 0, m * sizeof(double), ctx->stream);
     cudaMemsetAsync(w.theta[0], 0, m * sizeof(double), ctx->stream);
     cudaMemsetAsync(w.nu[1], 0, m * sizeof(double), ctx->stream);
@@ -377,6 +399,25 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
     double H = 0.0;
     for (double v : hr) H -= v * std::log(v);
     ctx->Hr = H;
+  }
+
+  // bf16 copies for the tensor-core sweeps; the float32 kernels (K pass, prime pass,
+  // gradient) then read the float32 copies of the rounded points, so every kernel
+  // solves the problem of the rounded points
+  if (ctx->prec == LAMP_PREC_BF16_TC) {
+    if ((rc = dalloc(ctx, reinterpret_cast<uint16_t**>(&ctx->xb), n_pad * 64))) return bail(rc);
+    if ((rc = dalloc(ctx, reinterpret_cast<uint16_t**>(&ctx->yb), m_pad * 64))) return bail(rc);
+    if ((rc = dalloc(ctx, &ctx->xr, n * (size_t)k.d))) return bail(rc);
+    if ((rc = dalloc(ctx, &ctx->yr, m * (size_t)k.d))) return bail(rc);
+    cudaError_t e = tc_convert(in.x, k.n, k.d, ctx->xr, ctx->xb, ctx->stream);
+    if (e == cudaSuccess) e = tc_convert(in.y, k.m, k.d, ctx->yr, ctx->yb, ctx->stream);
+    if (e == cudaSuccess) e = tc_make_map(ctx->map_x, ctx->xb, (int64_t)n_pad);
+    if (e == cudaSuccess) e = tc_make_map(ctx->map_y, ctx->yb, (int64_t)m_pad);
+    if (e != cudaSuccess) return bail(fail(ctx, LAMP_E_CUDA, "bf16 setup: %s", cudaGetErrorString(e)));
+    in.x = ctx->xr;
+    in.y = ctx->yr;
+    g.map_x = ctx->map_x;
+    g.map_y = ctx->map_y;
   }
 
   // cost scale and K = ||C||_inf of the cost the kernels use
@@ -507,6 +548,11 @@ extern "C" int lamp_solve(lamp_ctx* ctx, lamp_result* out) {
   }
   fill_result(ctx, out);
   const DevState& d = *ctx->host_dev;
+  if (d.status == LAMP_E_TIMEOUT) {
+    if (out) out->status = LAMP_E_TIMEOUT;
+    return fail(ctx, LAMP_E_TIMEOUT, "a device-side wait ran out of its iteration budget at iteration %lld",
+                (long long)d.t);
+  }
   if (d.status != 0) {
     if (out) out->status = LAMP_E_NUMERIC;
     return fail(ctx, LAMP_E_NUMERIC, "non-finite or out-of-range sum at iteration %lld", (long long)d.t);
@@ -563,6 +609,7 @@ extern "C" int lamp_objective(lamp_ctx* ctx, double out[8]) {
   out[5] = (k.eta == 0.0 && d.t >= 1) ? 4.0 * k.K * d.res + 2.0 * k.K * ctx->log_m / (double)d.t : NAN;
   out[6] = NAN;
   out[7] = k.K;
+  if (d.status == LAMP_E_TIMEOUT) return fail(ctx, LAMP_E_TIMEOUT, "a device-side wait ran out of its budget");
   if (d.status != 0) return fail(ctx, LAMP_E_NUMERIC, "non-finite or out-of-range sum");
   return LAMP_OK;
 }
@@ -638,6 +685,10 @@ extern "C" int lamp_step_host(lamp_ctx* ctx, const float* C_or_x, const float* y
     CK(cudaMemcpyAsync(ctx->own_b, y, (size_t)k.m * k.d * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->own_r, r, k.n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->own_c, c, k.m * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  if (ctx->prec == LAMP_PREC_BF16_TC) {
+    CK(tc_convert(ctx->own_a, k.n, k.d, ctx->xr, ctx->xb, ctx->stream));
+    CK(tc_convert(ctx->own_b, k.m, k.d, ctx->yr, ctx->yb, ctx->stream));
+  }
   int rc = lamp_iterate(ctx, iters);
   if (rc) return rc;
   CK(cudaMemcpyAsync(&ctx->host_dev->res, &ctx->w.dev->res, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));

@@ -185,6 +185,8 @@ struct Work {
 
 // Launch geometry chosen at create time.
 struct Geometry {
+  const void* map_x;  // tensor maps of the bf16 point copies (LAMP_PREC_BF16_TC), else null
+  const void* map_y;
   int sms;
   int rows_split;   // inner splits of the row sweep
   int cols_split;   // inner splits of the column sweep
@@ -212,6 +214,16 @@ cudaError_t launch_prime(const Inputs& in, const Consts& k, const Work& w, const
 cudaError_t launch_iteration(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
                              cudaStream_t st);
 void prepare_kernels();
+// tcgen05 path (lamp_tc.cu)
+size_t tc_smem_bytes();
+int64_t tc_pad(int64_t v);
+cudaError_t tc_convert(const float* P, int64_t np, int d, float* Pr, void* Pb, cudaStream_t st);
+cudaError_t tc_fill_pads(float4* a, int64_t from, int64_t to, cudaStream_t st);
+cudaError_t tc_make_map(void* map_out, const void* base, int64_t rows_pad);
+cudaError_t tc_prepare();
+int tc_blocks_per_sm(int which);
+cudaError_t tc_launch_sweep(bool rows, const void* map_x, const void* map_y, const Work& w, const Consts& k,
+                            int splits, cudaStream_t st);
 cudaError_t launch_iteration_part(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
                                   int part, cudaStream_t st);
 int tile_outer_cols(const Consts& k, int prec);

@@ -928,13 +928,16 @@ cudaError_t launch_prime(const Inputs& in, const Consts& k, const Work& w, const
 cudaError_t launch_iteration_part(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
                                   int part, cudaStream_t st) {
   const int rb = (int)cdiv(k.n, kThreads);
+  const bool tcpath = prec == 1 /* LAMP_PREC_BF16_TC */;
   switch (part) {
     case 0:
+      if (tcpath) return tc_launch_sweep(true, g.map_x, g.map_y, w, k, g.rows_split, st);
       return launch_row_sweep(in, k, w, g, M_ROWSUM, st);
     case 1:
       k_row_fin<<<rb, kThreads, 0, st>>>(w, g.rows_split, in.r, k);
       return cudaGetLastError();
     case 2:
+      if (tcpath) return tc_launch_sweep(false, g.map_x, g.map_y, w, k, g.cols_split, st);
       return launch_col_sweep(in, k, w, g, st);
     default:
       k_col_fin<<<(unsigned)cdiv(k.m, kThreads), kThreads, 0, st>>>(w, g.cols_split, in.c, rb, k);

@@ -49,6 +49,7 @@ __all__ = [
     "points_problem",
     "dense_problem",
     "WORKLOADS",
+    "bf16_round",
 ]
 
 
@@ -81,6 +82,14 @@ class Workload:
 
 def _rng(seed: int) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(seed))
+
+
+def bf16_round(a: np.ndarray) -> np.ndarray:
+    """Round float32 values to the nearest bfloat16 (ties to even), returned as float32:
+    the points a bf16 tensor-core path actually multiplies."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).reshape(np.shape(a))
 
 
 def uniform_marginal(n: int) -> np.ndarray:
