@@ -278,6 +278,35 @@ def run_gpu(args, rank, world):
                "d2h_bytes_per_step": int(8 + 8 * m), "steps": args.e2e_steps}
 
     info = {}
+    if rank == 0 and args.prec == "bf16_tc" and w.kind != "dense" and not args.no_fp32_compare:
+        # the plain float32 path on the same problem, same timing protocol
+        s32 = L.Lamp(r, c, x=x, y=y, cost_scale=w.cost_scale, **dict(params, prec="fp32"))
+        for _ in range(args.warmup):
+            s32.iterate(1)
+        torch.cuda.synchronize()
+        ev32 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.fp32_steps)]
+        for i in range(args.fp32_steps):
+            flush.zero_()
+            ev32[i][0].record(stream)
+            s32.iterate(1)
+            ev32[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms32 = sum(a.elapsed_time(b) for a, b in ev32) / args.fp32_steps
+        k32 = s32.time_kernels(3)
+        fp32 = {"value": n * m / (ms32 / 1e3), "ms_per_step": ms32, "kernel_ms": k32}
+        if args.ttt:
+            s32b = L.Lamp(r, c, x=x, y=y, cost_scale=w.cost_scale, max_iter=args.ttt_max_iter,
+                          **dict(params, prec="fp32"))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rr = s32b.solve()
+            fp32["time_to_tol"] = {"seconds": time.perf_counter() - t0, "iters": rr["iters"],
+                                   "infeas": rr["infeas"], "converged": rr["converged"], "tol": w.tol}
+            fp32["cost_at_tol"] = s32b.objective()["cost"]
+            s32b.close()
+        s32.close()
+        info["fp32_path"] = fp32
     if rank == 0 and args.ttt:
         # time to infeasibility <= tol from the Alg. 2 start, through lamp_solve
         s2 = L.Lamp(r, c, x=x, y=y, cost_scale=w.cost_scale, max_iter=args.ttt_max_iter,
@@ -288,6 +317,7 @@ def run_gpu(args, rank, world):
         el = time.perf_counter() - t0
         info["time_to_tol"] = {"seconds": el, "iters": res["iters"], "infeas": res["infeas"],
                                "converged": res["converged"], "tol": w.tol}
+        info["cost_at_tol"] = s2.objective()["cost"]
         s2.close()
 
     if rank != 0:
@@ -295,15 +325,23 @@ def run_gpu(args, rank, world):
             dist.destroy_process_group()
         return
     peaks, src = load_peaks()
-    sweep_ms = max(kern_ms[0], kern_ms[2])
     dom = 0 if kern_ms[0] >= kern_ms[2] else 2
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
     if bytes_per_entry:
         achieved = n * m * bytes_per_entry / (kern_ms[dom] / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None}
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "what": "stored C bytes of the " + ("row" if dom == 0 else "column") + " sweep"}
+    elif args.prec == "bf16_tc":
+        rate = L.measure_ex2_rate()
+        peak = sms * rate * mhz * 1e6 / 1e12
+        achieved = n * m * 2 / (kern_ms[dom] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tex2/s", "frac": achieved / peak,
+                "traffic": None,
+                "what": "MUFU ex2 of the " + ("row" if dom == 0 else "column") + " sweep (2 ex2 per entry: streams A, B)",
+                "peak_source": f"{sms} SMs x {rate:.2f} ex2/clk/SM (measured, lamp_measure_ex2_rate) x {mhz:.0f} MHz"}
     else:
-        mhz = float(peaks.get("sm_max_mhz", 2070.0))
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
         peak = sms * 128 * 2 * mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flop x max SM clock
         achieved = n * m * flops_per_entry / (kern_ms[dom] / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -321,7 +359,7 @@ def run_gpu(args, rank, world):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else "bf16-in/f32",
+        "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else "bf16 x.y, f32 accumulate and exp",
         "data": "synthetic",
         "config": {"workload": args.workload, "n": n, "m": m, "d": w.d, "eta": w.eta, "prec": args.prec,
                    "cost": w.kind, "l2": "flushed between steps (256 MB write)",
@@ -344,15 +382,21 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="highdim")
     ap.add_argument("--n", type=int, default=None, help="override n = m (profiling captures only)")
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16_tc"])
+    ap.add_argument("--prec", default=None, choices=["fp32", "bf16_tc"],
+                    help="default: bf16_tc for point clouds with d > 8, fp32 otherwise")
+    ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--fp32-steps", type=int, default=5)
     ap.add_argument("--check-every", type=int, default=50)
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--ttt", action="store_true", help="also measure time to infeasibility <= tol")
+    ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-infeasibility measurement")
     ap.add_argument("--ttt-max-iter", type=int, default=200000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-points", type=int, default=2048)
     args = ap.parse_args()
+    args.ttt = not args.no_ttt
+    if args.prec is None:
+        args.prec = "bf16_tc" if args.workload == "highdim" else "fp32"
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.warmup < 3 and args.impl == "gpu":

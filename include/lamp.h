@@ -203,6 +203,13 @@ LAMP_API int lamp_create_owned(lamp_ctx** out, const lamp_problem* host_prob, co
  * Synchronises.  iters >= 1. */
 LAMP_API int lamp_time_kernels(lamp_ctx* ctx, int64_t iters, double* ms_out);
 
+/* Measurement helper with no counterpart in the paper: the sustained MUFU ex2
+ * rate of the current device in results per SM per clock (dependent chains of
+ * ex2.approx.ftz.f32 on every SM, timed with the SMs' cycle counters).  It is
+ * the denominator of the roofline of the tensor-core sweeps.  Allocates and
+ * frees two small device buffers; synchronises. */
+LAMP_API int lamp_measure_ex2_rate(double* ex2_per_clk_per_sm);
+
 /* Number of kernel launches one iteration issues (for launch accounting). */
 LAMP_API int64_t lamp_launches_per_iteration(const lamp_ctx* ctx);
 

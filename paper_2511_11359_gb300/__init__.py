@@ -51,7 +51,7 @@ EXPORTED_SYMBOLS = [
     "lamp_params_default", "lamp_create", "lamp_solve", "lamp_iterate", "lamp_objective", "lamp_grad",
     "lamp_get_state", "lamp_set_state", "lamp_step_host", "lamp_create_owned",
     "lamp_launches_per_iteration", "lamp_last_error", "lamp_destroy", "lamp_time_kernels",
-    "lamp_marginals_noalloc",
+    "lamp_marginals_noalloc", "lamp_measure_ex2_rate",
 ]
 
 library_path = Path(__file__).resolve().parent / "liblamp.so"
@@ -148,6 +148,15 @@ def default_params(**kw) -> _Params:
             v = {"fp32": PREC_FP32, "bf16_tc": PREC_BF16_TC}[v]
         setattr(p, k, v)
     return p
+
+
+def measure_ex2_rate() -> float:
+    """Sustained ex2 results per SM per clock of the current device (lamp_measure_ex2_rate)."""
+    v = ctypes.c_double()
+    L = _get_lib()
+    L.lamp_measure_ex2_rate.argtypes = [ctypes.POINTER(ctypes.c_double)]
+    _check(L.lamp_measure_ex2_rate(ctypes.byref(v)))
+    return v.value
 
 
 def _ptr(t) -> int:

@@ -1,18 +1,20 @@
 // tcgen05 (5th-generation tensor core) sweeps of the LAMP hot path for the
 // squared-Euclidean cost in dot form, BF16 points, FP32 accumulation in TMEM.
 //
-// Both sweeps of an iteration (row sums G1, column sums G2; Section 4.1) issue
-// the SAME MMA for every (row tile, column tile) pair,
-//     D[128 rows x 128 cols] = Xb[rows, 0:64] * Yb[cols, 0:64]^T
-// (A = 128 points of x, B = 128 points of y, both K-major bf16 tiles staged by
-// TMA with 128-byte swizzle), so that the z = x.y values the two sweeps see are
-// bit-identical and the column sweep's normalisation matches the row sweep's
-// sums exactly.  G1 keeps its x tile fixed and streams y tiles; G2 keeps its y
-// tile fixed and streams x tiles.
+// The row sweep G1 computes, per 128-row x tile (fixed) and 128-column y tile
+// (streamed), D = Xb[rows, 0:64] * Yb[cols, 0:64]^T; the column sweep G2 computes
+// D' = Yb[cols] * Xb[rows]^T with the y tile fixed and x tiles streamed (A and B
+// are 128 x 64 K-major bf16 tiles staged by TMA with 128-byte swizzle).  With
+// bf16 operands every product is exact in fp32 and the MMA's accumulation does
+// not depend on which operand is A: D'[j][i] and D[i][j] are bit-identical, so
+// the column sweep's exponents equal the row sweep's and its normalisation
+// matches the row sums exactly.  In both sweeps one thread owns one TMEM lane
+// (a row of D in G1, a column of X in G2) and accumulates in registers.
 //
-// CTA = 6 warps: warps 0-3 read TMEM (warp w owns lanes 32w..32w+31, one row of
-// D per thread) and do the exponent / ex2 / reduction epilogue, warp 4 issues
-// TMA loads, warp 5 issues tcgen05.mma.  Two TMEM accumulators (2 x 128 columns)
+// CTA = 10 warps: warps 0-7 read TMEM (warp w owns lanes 32(w%4).. and columns
+// [64 (w/4), 64 (w/4) + 64) of each 128-column accumulator) and run the exponent /
+// ex2 / accumulation epilogue with packed f32x2 arithmetic over pairs of entries;
+// warp 8 issues TMA loads, warp 9 issues tcgen05.mma.  Two TMEM accumulators (2 x 128 columns)
 // let the MMA of tile i+1 overlap the epilogue of tile i; a 4-stage shared-memory
 // ring feeds the streamed operand.
 //
@@ -35,7 +37,11 @@ constexpr int kTile = 128;       // rows per A tile = columns per B tile = MMA M
 constexpr int kK = 64;           // K extent (points zero-padded to 64 coordinates)
 constexpr int kStages = 4;       // streamed-operand ring
 constexpr int kTileBytes = kTile * kK * 2;  // 16 KiB per bf16 tile
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;      // two warps per TMEM lane quadrant, each takes half the columns
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kProducerWarp = kEpiWarps;
+constexpr int kMmaWarp = kEpiWarps + 1;
+constexpr int kThreads = (kEpiWarps + 2) * 32;
 constexpr uint32_t kTmemCols = 256;         // two 128-column FP32 accumulators
 constexpr uint32_t kWaitLimit = 1u << 24;   // bounded spin on every mbarrier
 constexpr int kTimeoutStatus = 6;           // LAMP_E_TIMEOUT
@@ -155,6 +161,58 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// packed pairs of floats (fma / add / mul .rn.f32x2: two IEEE round-to-nearest
+// operations per instruction, lane by lane identical to the scalar ones)
+__device__ __forceinline__ uint64_t pk(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 upk(uint64_t v) {
+  float2 f;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(f.x), "=f"(f.y) : "l"(v));
+  return f;
+}
+__device__ __forceinline__ uint64_t f2fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2add(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// 2^v for a pair of entries: v = al z + (ah z + o), o = -(Rq + Bq) exact (see lamp_common.cuh)
+__device__ __forceinline__ uint64_t exp2_pair(uint64_t ah2, uint64_t al2, uint64_t z2, uint64_t o2) {
+  const float2 v = upk(f2fma(al2, z2, f2fma(ah2, z2, o2)));
+  return pk(ex2(v.x), ex2(v.y));
+}
+
+// barrier over the epilogue threads (named barrier 1) returning the OR of `v`
+// across them, so that every epilogue warp takes the same branch
+__device__ __forceinline__ bool epi_bar_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n"
+      ".reg .pred p, q;\n"
+      "setp.ne.u32 p, %1, 0;\n"
+      "bar.red.or.pred q, 1, %2, p;\n"
+      "selp.u32 %0, 1, 0, q;\n"
+      "}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(kEpiThreads)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
+
 // Shared-memory matrix descriptor of a K-major bf16 tile written by TMA with
 // 128-byte swizzle: rows of 128 bytes, 8-row (1024-byte) swizzle atoms, so the
 // stride between 8-row groups is 1024 bytes; the leading offset is unused for
@@ -179,25 +237,9 @@ __host__ __device__ constexpr uint32_t idesc_bf16_128x128() {
          | ((uint32_t)(kTile >> 4) << 24); // M >> 4
 }
 
-// exchange-and-add butterfly: on entry every lane holds v[0..31] for 32 columns
-// (its own row); on exit lane l holds in v[0] the sum over the 32 lanes of column l.
-__device__ __forceinline__ float lane_column_sum(float (&v)[32], int lane) {
-#pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) {
-    const bool upper = (lane & off) != 0;
-#pragma unroll
-    for (int i = 0; i < off; ++i) {
-      const float send = upper ? v[i] : v[i + off];
-      const float keep = upper ? v[i + off] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-    }
-  }
-  return v[0];
-}
-
 // ROWS = true: G1 (fixed x tile, streamed y tiles, per-row sums of both streams)
-// ROWS = false: G2 (fixed y tile, streamed x tiles, per-column sums of both streams and
-// of z * X for <C, X>)
+// ROWS = false: G2 (fixed y tile, streamed x tiles, per-column sums of both streams
+// and of z X for <C, X>)
 template <bool ROWS>
 __global__ void __launch_bounds__(kThreads, 2)
 k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_y, const Work w,
@@ -210,8 +252,10 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
   unsigned char* sFixed = smem;
   unsigned char* sStream = smem + kTileBytes;
   Bars* B = reinterpret_cast<Bars*>(smem + kTileBytes * (1 + kStages));
-  float* sColOff = reinterpret_cast<float*>(B + 1);         // G2: {BqA, BqB} x 128
-  double* sRed = reinterpret_cast<double*>(sColOff + 2 * kTile);  // G2: [4 warps][3][128]
+  // per streamed tile, double-buffered: for each pair of entries p, two float4
+  //   [0] = {-offA_2p, -offA_2p+1, wgtA_2p, wgtA_2p+1}, [1] = the same for stream B
+  // (G1: column offsets / weights w_j; G2: row offsets / weights q_i)
+  float4* sPair = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(B) + 128);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -232,19 +276,10 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&B->tmem_full[b], 1);
-      mbar_init(&B->tmem_empty[b], 128);
+      mbar_init(&B->tmem_empty[b], kEpiThreads);
     }
     B->err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (!ROWS) {
-    // fixed column offsets of this CTA's 128 columns (BqA, BqB); padded columns hold +inf
-    const float4* __restrict__ colq = w.colq[cur];
-    for (int t = threadIdx.x; t < kTile; t += blockDim.x) {
-      const float4 q = colq[fixed0 + t];
-      sColOff[2 * t] = q.x;
-      sColOff[2 * t + 1] = q.z;
-    }
   }
   if (warp == 0) {
     tmem_alloc(&B->tmem_base, kTmemCols);
@@ -255,7 +290,7 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
   tc_fence_after();
   const uint32_t tmem = B->tmem_base;
 
-  if (warp == 4) {
+  if (warp == kProducerWarp) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
       int issued = 0;
@@ -275,8 +310,8 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
           mbar_drain(&B->full[i % kStages], (i / kStages) & 1);
       }
     }
-  } else if (warp == 5) {
-    // ---------------- MMA issuer ----------------
+  } else if (warp == kMmaWarp) {
+    // ---------------- MMA issuer: D[buffer] = A(fixed) * B(streamed)^T ----------------
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16_128x128();
       int issued = 0;
@@ -289,11 +324,10 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
           if (!mbar_wait(&B->full[s], (i / kStages) & 1, B, dev)) break;
           if (i >= 2 && !mbar_wait(&B->tmem_empty[b], ((i >> 1) - 1) & 1, B, dev)) break;
           tc_fence_after();
-          const uint32_t aBase = ROWS ? sF : sS + s * kTileBytes;
-          const uint32_t bBase = ROWS ? sS + s * kTileBytes : sF;
+          const uint32_t bBase = sS + s * kTileBytes;
 #pragma unroll
           for (int kk = 0; kk < kK / 16; ++kk)
-            umma_bf16(tmem + b * kTile, sdesc_sw128(aBase + kk * 32), sdesc_sw128(bBase + kk * 32), idesc, kk > 0);
+            umma_bf16(tmem + b * kTile, sdesc_sw128(sF + kk * 32), sdesc_sw128(bBase + kk * 32), idesc, kk > 0);
           umma_commit(&B->empty[s]);
           umma_commit(&B->tmem_full[b]);
           issued = i + 1;
@@ -305,109 +339,105 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
       }
     }
   } else {
-    // ---------------- epilogue: warps 0-3, thread = row of D ----------------
+    // ---------------- epilogue: warps 0-7; lane index t, column half h ----------------
+    const int t = (warp & 3) * 32 + lane;  // TMEM lane = row of D owned (0..127)
+    const int h = warp >> 2;               // which 64 of the 128 accumulator columns
     const SweepParams sp = make_sweep_params(dev->kappa, k);
-    const float ahA = sp.ahA, alA = sp.alA, ahB = sp.ahB, alB = sp.alB;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const uint64_t ahA2 = pk(sp.ahA, sp.ahA), alA2 = pk(sp.alA, sp.alA);
+    const uint64_t ahB2 = pk(sp.ahB, sp.ahB), alB2 = pk(sp.alB, sp.alB);
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    // this thread's own offsets (G1: its row's shifts; G2: its column's offsets), negated
+    uint64_t ownA2, ownB2;
+    const int64_t own = fixed0 + t;
     if (ROWS) {
-      int64_t row = fixed0 + warp * 32 + lane;
-      const int64_t rowc = row < n ? row : n - 1;
-      const float2 rq = w.rowshift[cur][rowc];
-      const float4* __restrict__ colq = w.colq[cur];
-      float hiA = 0.f, loA = 0.f, hiB = 0.f, loB = 0.f;
-      for (int i = 0; i < ntiles; ++i) {
-        const int b = i & 1;
-        // warp-uniform decision before the .sync.aligned TMEM loads
-        if (!__all_sync(0xffffffffu, mbar_wait(&B->tmem_full[b], (i >> 1) & 1, B, dev))) break;
-        tc_fence_after();
-        const int64_t col0 = (it0 + i) * kTile;
-#pragma unroll 1
-        for (int c = 0; c < kTile / 32; ++c) {
-          uint32_t v[32];
-          tmem_ld32(tmem + lane_base + b * kTile + c * 32, v);
-          tmem_wait_ld();
-          float sA = 0.f, sB = 0.f;
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const float z = __uint_as_float(v[j]);
-            const float4 cq = __ldg(colq + col0 + c * 32 + j);  // padded columns: {+inf, 0, +inf, 0}
-            const float vA = __fmaf_rn(alA, z, __fmaf_rn(ahA, z, -(rq.x + cq.x)));
-            const float vB = __fmaf_rn(alB, z, __fmaf_rn(ahB, z, -(rq.y + cq.z)));
-            sA = __fmaf_rn(ex2(vA), cq.y, sA);
-            sB = __fmaf_rn(ex2(vB), cq.w, sB);
-          }
-          ff_add(hiA, loA, sA);
-          ff_add(hiB, loB, sB);
-        }
-        tc_fence_before();
-        mbar_arrive(&B->tmem_empty[b]);
-      }
-      if (row < n && !*(volatile int*)&B->err) {
-        w.rowpart[((int64_t)blockIdx.y * 2 + 0) * n + row] = (double)hiA + (double)loA;
-        w.rowpart[((int64_t)blockIdx.y * 2 + 1) * n + row] = (double)hiB + (double)loB;
-      }
+      const float2 rq = w.rowshift[cur][own < n ? own : n - 1];
+      ownA2 = pk(-rq.x, -rq.x);
+      ownB2 = pk(-rq.y, -rq.y);
     } else {
-      // per-lane accumulators of the columns this lane ends up owning after the butterfly
-      float hA[kTile / 32], lA[kTile / 32], hB[kTile / 32], lB[kTile / 32], hC[kTile / 32], lC[kTile / 32];
-#pragma unroll
-      for (int c = 0; c < kTile / 32; ++c) hA[c] = lA[c] = hB[c] = lB[c] = hC[c] = lC[c] = 0.f;
-      for (int i = 0; i < ntiles; ++i) {
-        const int b = i & 1;
-        const int64_t row = (it0 + i) * kTile + warp * 32 + lane;
-        const float4 rd = w.g2row[row];  // padded rows: {+inf, 0, +inf, 0}
-        if (!__all_sync(0xffffffffu, mbar_wait(&B->tmem_full[b], (i >> 1) & 1, B, dev))) break;
-        tc_fence_after();
-#pragma unroll
-        for (int c = 0; c < kTile / 32; ++c) {
-          uint32_t v[32];
-          tmem_ld32(tmem + lane_base + b * kTile + c * 32, v);
-          tmem_wait_ld();
-          float p[32], pc[32];
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const float z = __uint_as_float(v[j]);
-            const float coA = sColOff[2 * (c * 32 + j)];
-            const float vA = __fmaf_rn(alA, z, __fmaf_rn(ahA, z, -(rd.x + coA)));
-            p[j] = ex2(vA) * rd.y;
-            pc[j] = z * p[j];
-          }
-          ff_add(hA[c], lA[c], lane_column_sum(p, lane));
-          ff_add(hC[c], lC[c], lane_column_sum(pc, lane));
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const float z = __uint_as_float(v[j]);
-            const float coB = sColOff[2 * (c * 32 + j) + 1];
-            const float vB = __fmaf_rn(alB, z, __fmaf_rn(ahB, z, -(rd.z + coB)));
-            p[j] = ex2(vB) * rd.w;
-          }
-          ff_add(hB[c], lB[c], lane_column_sum(p, lane));
-        }
-        tc_fence_before();
-        mbar_arrive(&B->tmem_empty[b]);
+      const float4 cq = w.colq[cur][own];  // padded columns: {+inf, 0, +inf, 0}
+      ownA2 = pk(-cq.x, -cq.x);
+      ownB2 = pk(-cq.z, -cq.z);
+    }
+    const float4* __restrict__ stream_src = ROWS ? w.colq[cur] : w.g2row;  // {off A, wgt A, off B, wgt B}
+    float hiA = 0.f, loA = 0.f, hiB = 0.f, loB = 0.f, hiC = 0.f, loC = 0.f;
+    for (int i = 0; i < ntiles; ++i) {
+      const int b = i & 1;
+      if (h == 0) {
+        // stage the streamed tile's offsets and weights as packed pairs
+        const float4 q = stream_src[(it0 + i) * kTile + t];  // padding: {+inf, 0, +inf, 0}
+        float* d = reinterpret_cast<float*>(sPair + (size_t)(b * (kTile / 2) + (t >> 1)) * 2);
+        const int o = t & 1;
+        d[0 + o] = -q.x;
+        d[2 + o] = q.y;
+        d[4 + o] = -q.z;
+        d[6 + o] = q.w;
       }
-      // cross-warp reduction of the 4 warps' column partials
+      const bool ok = mbar_wait(&B->tmem_full[b], (i >> 1) & 1, B, dev);
+      // staging barrier and epilogue-wide agreement on errors
+      if (epi_bar_or(!ok)) break;
+      tc_fence_after();
+      const float4* pr = sPair + (size_t)b * kTile;
+#pragma unroll 1
+      for (int cc = 0; cc < 2; ++cc) {
+        const int c = 2 * h + cc;
+        uint32_t v[32];
+        tmem_ld32(tmem + lane_base + b * kTile + c * 32, v);
+        tmem_wait_ld();
+        uint64_t accA[2] = {0ull, 0ull}, accB[2] = {0ull, 0ull}, accC[2] = {0ull, 0ull};
 #pragma unroll
-      for (int c = 0; c < kTile / 32; ++c) {
-        const int col = c * 32 + lane;
-        sRed[(warp * 3 + 0) * kTile + col] = (double)hA[c] + (double)lA[c];
-        sRed[(warp * 3 + 1) * kTile + col] = (double)hB[c] + (double)lB[c];
-        sRed[(warp * 3 + 2) * kTile + col] = (double)hC[c] + (double)lC[c];
+        for (int p = 0; p < 16; ++p) {
+          const float4 qa = pr[(c * 16 + p) * 2];
+          const float4 qb = pr[(c * 16 + p) * 2 + 1];
+          const uint64_t z2 = pk(__uint_as_float(v[2 * p]), __uint_as_float(v[2 * p + 1]));
+          const uint64_t eA = exp2_pair(ahA2, alA2, z2, f2add(ownA2, pk(qa.x, qa.y)));
+          const uint64_t eB = exp2_pair(ahB2, alB2, z2, f2add(ownB2, pk(qb.x, qb.y)));
+          if (ROWS) {
+            accA[p & 1] = f2fma(eA, pk(qa.z, qa.w), accA[p & 1]);
+          } else {
+            const uint64_t pA = f2mul(eA, pk(qa.z, qa.w));
+            accA[p & 1] = f2add(accA[p & 1], pA);
+            accC[p & 1] = f2fma(z2, pA, accC[p & 1]);
+          }
+          accB[p & 1] = f2fma(eB, pk(qb.z, qb.w), accB[p & 1]);
+        }
+        const float2 a2 = upk(f2add(accA[0], accA[1])), b2 = upk(f2add(accB[0], accB[1]));
+        ff_add(hiA, loA, a2.x + a2.y);
+        ff_add(hiB, loB, b2.x + b2.y);
+        if (!ROWS) {
+          const float2 c2 = upk(f2add(accC[0], accC[1]));
+          ff_add(hiC, loC, c2.x + c2.y);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&B->tmem_empty[b]);
+    }
+    // combine the two column halves of each lane (the stream ring is idle now: every
+    // loaded tile has been consumed by an MMA whose completion the epilogue waited for)
+    double* comb = reinterpret_cast<double*>(sStream);
+    if (h == 1) {
+      comb[t * 3 + 0] = (double)hiA + (double)loA;
+      comb[t * 3 + 1] = (double)hiB + (double)loB;
+      comb[t * 3 + 2] = (double)hiC + (double)loC;
+    }
+    epi_bar();
+    if (h == 0 && !*(volatile int*)&B->err) {
+      const double sA = (double)hiA + (double)loA + comb[t * 3 + 0];
+      const double sB = (double)hiB + (double)loB + comb[t * 3 + 1];
+      const double sC = (double)hiC + (double)loC + comb[t * 3 + 2];
+      if (ROWS) {
+        if (own < n) {
+          w.rowpart[((int64_t)blockIdx.y * 2 + 0) * n + own] = sA;
+          w.rowpart[((int64_t)blockIdx.y * 2 + 1) * n + own] = sB;
+        }
+      } else if (own < m) {
+        w.colpart[((int64_t)blockIdx.y * 3 + 0) * m + own] = sA;
+        w.colpart[((int64_t)blockIdx.y * 3 + 1) * m + own] = sB;
+        w.colpart[((int64_t)blockIdx.y * 3 + 2) * m + own] = sC;
       }
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (!ROWS && threadIdx.x < kTile && !*(volatile int*)&B->err) {
-    const int col = threadIdx.x;
-    const int64_t gcol = fixed0 + col;
-    if (gcol < m) {
-      for (int q = 0; q < 3; ++q) {
-        double s = 0.0;
-        for (int wi = 0; wi < 4; ++wi) s += sRed[(wi * 3 + q) * kTile + col];
-        w.colpart[((int64_t)blockIdx.y * 3 + q) * m + gcol] = s;
-      }
-    }
-  }
   if (warp == 0) {
     tc_fence_after();
     tmem_dealloc(tmem, kTmemCols);
@@ -436,8 +466,9 @@ __global__ void k_fill_pad4(float4* __restrict__ a, int64_t from, int64_t to) {
 }  // namespace tc
 
 size_t tc_smem_bytes() {
-  return 1024 /* alignment slack */ + (size_t)tc::kTileBytes * (1 + tc::kStages) + sizeof(tc::Bars) +
-         2 * tc::kTile * sizeof(float) + 4 * 3 * tc::kTile * sizeof(double);
+  // alignment slack + fixed tile + ring + barriers (128 bytes) + staged pairs (2 x 128 float4)
+  static_assert(sizeof(tc::Bars) <= 128, "barrier block");
+  return 1024 + (size_t)tc::kTileBytes * (1 + tc::kStages) + 128 + 2 * tc::kTile * sizeof(float4);
 }
 
 int64_t tc_pad(int64_t v) { return (v + tc::kTile - 1) / tc::kTile * tc::kTile; }
