@@ -341,6 +341,11 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
     if ((rc = dalloc(ctx, &w.rowshift[b], n))) return bail(rc);
   }
   if ((rc = dalloc(ctx, &w.g2row, n_pad))) return bail(rc);
+  if (ctx->prec == LAMP_PREC_BF16_TC) {
+    for (int b = 0; b < 2; ++b)
+      if ((rc = dalloc(ctx, &w.colq2[b], m_pad))) return bail(rc);
+    if ((rc = dalloc(ctx, &w.g2row2, n_pad))) return bail(rc);
+  }
   if ((rc = dalloc(ctx, &w.rowpart, (size_t)g.rows_split * std::max<size_t>(2, gradd) * n))) return bail(rc);
   if ((rc = dalloc(ctx, &w.colpart, (size_t)g.cols_split * std::max<size_t>(3, gradd) * m))) return bail(rc);
   if ((rc = dalloc(ctx, &w.logZ, n))) return bail(rc);
@@ -364,6 +369,11 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
     tc_fill_pads(w.colq[0], k.m, (int64_t)m_pad, ctx->stream);
     tc_fill_pads(w.colq[1], k.m, (int64_t)m_pad, ctx->stream);
     tc_fill_pads(w.g2row, k.n, (int64_t)n_pad, ctx->stream);
+    if (w.g2row2) {
+      tc_fill_pairs(w.colq2[0], (int64_t)m_pad, ctx->stream);
+      tc_fill_pairs(w.colq2[1], (int64_t)m_pad, ctx->stream);
+      tc_fill_pairs(w.g2row2, (int64_t)n_pad, ctx->stream);
+    }
     cudaMemsetAsync(w.nu[0], 0, m * sizeof(double), ctx->stream);
     cudaMemsetAsync(w.theta[0], 0, m * sizeof(double), ctx->stream);
     cudaMemsetAsync(w.nu[1], 0, m * sizeof(double), ctx->stream);

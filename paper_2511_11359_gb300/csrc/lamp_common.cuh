@@ -119,6 +119,17 @@ __host__ __device__ inline double quantize(double x, double g) {
 }
 
 #ifdef __CUDACC__
+// write entry e of a packed-pair array (layout described in Work)
+__device__ __forceinline__ void store_pair_entry(float4* __restrict__ a, int64_t e, float offA, float wA, float offB,
+                                                 float wB) {
+  float* fa = reinterpret_cast<float*>(a + (e >> 1) * 2);
+  const int h = (int)(e & 1);
+  fa[0 + h] = -offA;
+  fa[2 + h] = wA;
+  fa[4 + h] = -offB;
+  fa[6 + h] = wB;
+}
+
 // 2^x with the SFU (MUFU.EX2), flush-to-zero
 __device__ __forceinline__ float ex2(float x) {
   float y;
@@ -170,6 +181,11 @@ struct Work {
   float4* colq[2];     // per column {BqA, wA, BqB, wB}
   float2* rowshift[2]; // per row {RqA, RqB}
   float4* g2row;       // per row {RqA, qA, RqB, qB} for the column sweep
+  // the same data in the packed-pair layout read by the tensor-core sweeps (null when
+  // unused): for entries 2p, 2p+1 two float4, [2p] = {-offA_2p, -offA_2p+1, wgtA_2p,
+  // wgtA_2p+1} and [2p+1] = the same for stream B; padding halves hold {-inf, 0}
+  float4* colq2[2];
+  float4* g2row2;
   double* rowpart;     // [splits_rows][2][n] partial row sums
   double* colpart;     // [splits_cols][3][m] partial column sums (A, B, cost-weighted A)
   double* logZ;        // [n] natural-log normalisers of X^t
@@ -219,6 +235,7 @@ size_t tc_smem_bytes();
 int64_t tc_pad(int64_t v);
 cudaError_t tc_convert(const float* P, int64_t np, int d, float* Pr, void* Pb, cudaStream_t st);
 cudaError_t tc_fill_pads(float4* a, int64_t from, int64_t to, cudaStream_t st);
+cudaError_t tc_fill_pairs(float4* a, int64_t count, cudaStream_t st);
 cudaError_t tc_make_map(void* map_out, const void* base, int64_t rows_pad);
 cudaError_t tc_prepare();
 int tc_blocks_per_sm(int which);

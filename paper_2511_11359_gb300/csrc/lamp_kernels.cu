@@ -593,7 +593,9 @@ __global__ void k_init_cols(const Work w, const Consts k, int zero) {
   double wt = k.tau1 / sp.kapB;  // tau1 eta_{t+1}
   double nb = nu[j] + wt * (theta[j] - nu[j]);
   double sny = k.zdot ? k.s * ny[j] : 0.0;
-  colq[j] = column_data(nu[j], nb, sny, sp, k);
+  const float4 cd = column_data(nu[j], nb, sny, sp, k);
+  colq[j] = cd;
+  if (w.colq2[cur]) store_pair_entry(w.colq2[cur], j, cd.x, cd.y, cd.z, cd.w);
 }
 
 // row shifts from the prime pass' row maxima: Rq = round_g(max_j (a z_ij - Bq_j))
@@ -654,6 +656,7 @@ k_row_fin(const Work w, int splits, const double* __restrict__ r, const Consts k
     double ri = r[i];
     contrib = ri * lz;
     g2row[i] = make_float4(rq.x, (float)(ri / SA), rq.y, (float)(ri / SB));
+    if (w.g2row2) store_pair_entry(w.g2row2, i, rq.x, (float)(ri / SA), rq.y, (float)(ri / SB));
     // shifts of iteration t+1: stream A there has kappa_{t+1} (stream B here);
     // stream B there is extrapolated linearly in t.
     double tA = (double)rq.y + lsB;
@@ -719,9 +722,9 @@ k_col_fin(const Work w, int splits, const double* __restrict__ cvec, int rowbloc
       const double ca = cj + k.alpha / (double)k.m;  // c^alpha (Section 3.1)
       const double gj = 2.0 * k.tau2 * k.K / ca;
       const double ath = atanh(thj);
-      const double w = k.tau1 / sp.kapB;                 // tau1 eta_{t+1}
+      const double wt = k.tau1 / sp.kapB;                // tau1 eta_{t+1}
       const double thbar = tanh(gj * (A - cj) + ath);    // M_{tau2}(theta^t; p^{eta_t}(nu^t))
-      const double nun = nuj + w * (thbar - nuj);        // nu^{t+1}
+      const double nun = nuj + wt * (thbar - nuj);       // nu^{t+1}
       double thhat = tanh(gj * (B - cj) + ath);          // M_{tau2}(theta^t; p^{eta_{t+1}}(nubar^{t+1}))
       const double thn = fmin(fmax(thhat, -k.clipb), k.clipb);  // tclip
       nu_nxt[j] = nun;
@@ -731,7 +734,9 @@ k_col_fin(const Work w, int splits, const double* __restrict__ cvec, int rowbloc
       const double wn = k.tau1 / spn.kapB;
       const double nbn = nun + wn * (thn - nun);         // nubar^{t+2}
       const double sny = k.zdot ? k.s * ny[j] : 0.0;
-      colq_nxt[j] = column_data(nun, nbn, sny, spn, k);
+      const float4 cd = column_data(nun, nbn, sny, spn, k);
+      colq_nxt[j] = cd;
+      if (w.colq2[cur ^ 1]) store_pair_entry(w.colq2[cur ^ 1], j, cd.x, cd.y, cd.z, cd.w);
     }
   }
   res = warp_sum_d(res);

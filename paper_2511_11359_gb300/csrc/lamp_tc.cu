@@ -52,9 +52,13 @@ struct __align__(8) Bars {
   uint64_t empty[kStages];
   uint64_t tmem_full[2];
   uint64_t tmem_empty[2];
+  uint64_t pair_full[2];   // packed offsets / weights of the streamed tile landed (bulk copy)
+  uint64_t pair_empty[2];  // epilogue finished reading them
   uint32_t tmem_base;
   int err;
 };
+constexpr int kBarBytes = 256;
+static_assert(sizeof(Bars) <= kBarBytes, "barrier block");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -109,6 +113,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// plain (untiled) bulk copy global -> shared, completion counted on an mbarrier;
+// both addresses 16-byte aligned, size a multiple of 16
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
                : "memory");
@@ -146,20 +159,26 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                : "memory");
 }
 
-// 32 consecutive FP32 columns of this warp's 32 TMEM lanes, one lane per thread
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes, load and wait in ONE asm
+// statement: the destination registers of tcgen05.ld are written asynchronously until
+// tcgen05.wait::ld, and if the two were separate statements the compiler could copy
+// or spill those registers in between (it believes they are already final).
+__device__ __forceinline__ void tmem_ld32_wait(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
       "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
         "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
         "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
         "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-      : "r"(taddr));
+      : "r"(taddr)
+      : "memory");
 }
 
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 
 // packed pairs of floats (fma / add / mul .rn.f32x2: two IEEE round-to-nearest
 // operations per instruction, lane by lane identical to the scalar ones)
@@ -253,9 +272,10 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
   unsigned char* sStream = smem + kTileBytes;
   Bars* B = reinterpret_cast<Bars*>(smem + kTileBytes * (1 + kStages));
   // per streamed tile, double-buffered: for each pair of entries p, two float4
-  //   [0] = {-offA_2p, -offA_2p+1, wgtA_2p, wgtA_2p+1}, [1] = the same for stream B
-  // (G1: column offsets / weights w_j; G2: row offsets / weights q_i)
-  float4* sPair = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(B) + 128);
+  //   [2p] = {-offA_2p, -offA_2p+1, wgtA_2p, wgtA_2p+1}, [2p+1] = the same for stream B
+  // (G1: column offsets / weights w_j; G2: row offsets / weights q_i), copied by TMA
+  // from the packed-pair arrays the finalize kernels write
+  float4* sPair = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(B) + kBarBytes);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -277,6 +297,8 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
     for (int b = 0; b < 2; ++b) {
       mbar_init(&B->tmem_full[b], 1);
       mbar_init(&B->tmem_empty[b], kEpiThreads);
+      mbar_init(&B->pair_full[b], 1);
+      mbar_init(&B->pair_empty[b], kEpiThreads);
     }
     B->err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -293,21 +315,28 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
   if (warp == kProducerWarp) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
-      int issued = 0;
+      const float4* __restrict__ pair_src = ROWS ? w.colq2[cur] : w.g2row2;
+      int issued = 0, pissued = 0;
       mbar_expect_tx(&B->fixed_full, kTileBytes);
       tma_load_2d(sFixed, ROWS ? &map_x : &map_y, &B->fixed_full, 0, (int)fixed0);
       for (int i = 0; i < ntiles; ++i) {
         const int s = i % kStages;
+        const int b = i & 1;
         if (i >= kStages && !mbar_wait(&B->empty[s], ((i / kStages) & 1) ^ 1, B, dev)) break;
         mbar_expect_tx(&B->full[s], kTileBytes);
         tma_load_2d(sStream + s * kTileBytes, ROWS ? &map_y : &map_x, &B->full[s], 0, (int)((it0 + i) * kTile));
         issued = i + 1;
+        if (i >= 2 && !mbar_wait(&B->pair_empty[b], ((i >> 1) - 1) & 1, B, dev)) break;
+        mbar_expect_tx(&B->pair_full[b], kTile * sizeof(float4));
+        bulk_load(sPair + (size_t)b * kTile, pair_src + (it0 + i) * kTile, kTile * sizeof(float4), &B->pair_full[b]);
+        pissued = i + 1;
       }
       if (*(volatile int*)&B->err) {
         // error: let this thread's copies in flight land before the CTA exits
         mbar_drain(&B->fixed_full, 0);
         for (int i = issued - kStages < 0 ? 0 : issued - kStages; i < issued; ++i)
           mbar_drain(&B->full[i % kStages], (i / kStages) & 1);
+        for (int i = pissued - 2 < 0 ? 0 : pissued - 2; i < pissued; ++i) mbar_drain(&B->pair_full[i & 1], (i >> 1) & 1);
       }
     }
   } else if (warp == kMmaWarp) {
@@ -345,7 +374,7 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
     const SweepParams sp = make_sweep_params(dev->kappa, k);
     const uint64_t ahA2 = pk(sp.ahA, sp.ahA), alA2 = pk(sp.alA, sp.alA);
     const uint64_t ahB2 = pk(sp.ahB, sp.ahB), alB2 = pk(sp.alB, sp.alB);
-    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;  // TMEM lane field
     // this thread's own offsets (G1: its row's shifts; G2: its column's offsets), negated
     uint64_t ownA2, ownB2;
     const int64_t own = fixed0 + t;
@@ -358,58 +387,55 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
       ownA2 = pk(-cq.x, -cq.x);
       ownB2 = pk(-cq.z, -cq.z);
     }
-    const float4* __restrict__ stream_src = ROWS ? w.colq[cur] : w.g2row;  // {off A, wgt A, off B, wgt B}
     float hiA = 0.f, loA = 0.f, hiB = 0.f, loB = 0.f, hiC = 0.f, loC = 0.f;
+    // process 16 accumulator columns (8 pairs) starting at column col of the tile
+    auto half_chunk = [&](const uint32_t (&v)[16], const float4* pr, int col) {
+      uint64_t accA[2] = {0ull, 0ull}, accB[2] = {0ull, 0ull}, accC[2] = {0ull, 0ull};
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        const float4 qa = pr[col + 2 * p];
+        const float4 qb = pr[col + 2 * p + 1];
+        const uint64_t z2 = pk(__uint_as_float(v[2 * p]), __uint_as_float(v[2 * p + 1]));
+        const uint64_t eA = exp2_pair(ahA2, alA2, z2, f2add(ownA2, pk(qa.x, qa.y)));
+        const uint64_t eB = exp2_pair(ahB2, alB2, z2, f2add(ownB2, pk(qb.x, qb.y)));
+        if (ROWS) {
+          accA[p & 1] = f2fma(eA, pk(qa.z, qa.w), accA[p & 1]);
+        } else {
+          const uint64_t pA = f2mul(eA, pk(qa.z, qa.w));
+          accA[p & 1] = f2add(accA[p & 1], pA);
+          accC[p & 1] = f2fma(z2, pA, accC[p & 1]);
+        }
+        accB[p & 1] = f2fma(eB, pk(qb.z, qb.w), accB[p & 1]);
+      }
+      const float2 a2 = upk(f2add(accA[0], accA[1])), b2 = upk(f2add(accB[0], accB[1]));
+      ff_add(hiA, loA, a2.x + a2.y);
+      ff_add(hiB, loB, b2.x + b2.y);
+      if (!ROWS) {
+        const float2 c2 = upk(f2add(accC[0], accC[1]));
+        ff_add(hiC, loC, c2.x + c2.y);
+      }
+    };
     for (int i = 0; i < ntiles; ++i) {
       const int b = i & 1;
-      if (h == 0) {
-        // stage the streamed tile's offsets and weights as packed pairs
-        const float4 q = stream_src[(it0 + i) * kTile + t];  // padding: {+inf, 0, +inf, 0}
-        float* d = reinterpret_cast<float*>(sPair + (size_t)(b * (kTile / 2) + (t >> 1)) * 2);
-        const int o = t & 1;
-        d[0 + o] = -q.x;
-        d[2 + o] = q.y;
-        d[4 + o] = -q.z;
-        d[6 + o] = q.w;
-      }
-      const bool ok = mbar_wait(&B->tmem_full[b], (i >> 1) & 1, B, dev);
-      // staging barrier and epilogue-wide agreement on errors
-      if (epi_bar_or(!ok)) break;
+      bool ok = mbar_wait(&B->pair_full[b], (i >> 1) & 1, B, dev);
+      ok = ok && mbar_wait(&B->tmem_full[b], (i >> 1) & 1, B, dev);
+      // warp-uniform decision before the .sync.aligned TMEM loads
+      if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
       const float4* pr = sPair + (size_t)b * kTile;
+      // this warp's 64 columns as two 32-column loads (each with its wait); other warps
+      // of the SM sub-partition cover the TMEM latency
+      const uint32_t tbase = tmem + lane_base + b * kTile + h * 64;
 #pragma unroll 1
-      for (int cc = 0; cc < 2; ++cc) {
-        const int c = 2 * h + cc;
+      for (int c = 0; c < 2; ++c) {
         uint32_t v[32];
-        tmem_ld32(tmem + lane_base + b * kTile + c * 32, v);
-        tmem_wait_ld();
-        uint64_t accA[2] = {0ull, 0ull}, accB[2] = {0ull, 0ull}, accC[2] = {0ull, 0ull};
-#pragma unroll
-        for (int p = 0; p < 16; ++p) {
-          const float4 qa = pr[(c * 16 + p) * 2];
-          const float4 qb = pr[(c * 16 + p) * 2 + 1];
-          const uint64_t z2 = pk(__uint_as_float(v[2 * p]), __uint_as_float(v[2 * p + 1]));
-          const uint64_t eA = exp2_pair(ahA2, alA2, z2, f2add(ownA2, pk(qa.x, qa.y)));
-          const uint64_t eB = exp2_pair(ahB2, alB2, z2, f2add(ownB2, pk(qb.x, qb.y)));
-          if (ROWS) {
-            accA[p & 1] = f2fma(eA, pk(qa.z, qa.w), accA[p & 1]);
-          } else {
-            const uint64_t pA = f2mul(eA, pk(qa.z, qa.w));
-            accA[p & 1] = f2add(accA[p & 1], pA);
-            accC[p & 1] = f2fma(z2, pA, accC[p & 1]);
-          }
-          accB[p & 1] = f2fma(eB, pk(qb.z, qb.w), accB[p & 1]);
-        }
-        const float2 a2 = upk(f2add(accA[0], accA[1])), b2 = upk(f2add(accB[0], accB[1]));
-        ff_add(hiA, loA, a2.x + a2.y);
-        ff_add(hiB, loB, b2.x + b2.y);
-        if (!ROWS) {
-          const float2 c2 = upk(f2add(accC[0], accC[1]));
-          ff_add(hiC, loC, c2.x + c2.y);
-        }
+        tmem_ld32_wait(tbase + c * 32, v);
+        half_chunk(*reinterpret_cast<const uint32_t(*)[16]>(&v[0]), pr, h * 64 + c * 32);
+        half_chunk(*reinterpret_cast<const uint32_t(*)[16]>(&v[16]), pr, h * 64 + c * 32 + 16);
       }
       tc_fence_before();
       mbar_arrive(&B->tmem_empty[b]);
+      mbar_arrive(&B->pair_empty[b]);
     }
     // combine the two column halves of each lane (the stream ring is idle now: every
     // loaded tile has been consumed by an MMA whose completion the epilogue waited for)
@@ -463,12 +489,17 @@ __global__ void k_fill_pad4(float4* __restrict__ a, int64_t from, int64_t to) {
   if (i < to) a[i] = make_float4(INFINITY, 0.f, INFINITY, 0.f);
 }
 
+// packed-pair arrays: every half starts as padding {-off = -inf, wgt = 0}
+__global__ void k_fill_pairs(float4* __restrict__ a, int64_t count) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) a[i] = make_float4(-INFINITY, -INFINITY, 0.f, 0.f);
+}
+
 }  // namespace tc
 
 size_t tc_smem_bytes() {
-  // alignment slack + fixed tile + ring + barriers (128 bytes) + staged pairs (2 x 128 float4)
-  static_assert(sizeof(tc::Bars) <= 128, "barrier block");
-  return 1024 + (size_t)tc::kTileBytes * (1 + tc::kStages) + 128 + 2 * tc::kTile * sizeof(float4);
+  // alignment slack + fixed tile + ring + barriers + packed pairs (2 x 128 float4)
+  return 1024 + (size_t)tc::kTileBytes * (1 + tc::kStages) + tc::kBarBytes + 2 * tc::kTile * sizeof(float4);
 }
 
 int64_t tc_pad(int64_t v) { return (v + tc::kTile - 1) / tc::kTile * tc::kTile; }
@@ -484,6 +515,12 @@ cudaError_t tc_convert(const float* P, int64_t np, int d, float* Pr, void* Pb, c
 cudaError_t tc_fill_pads(float4* a, int64_t from, int64_t to, cudaStream_t st) {
   if (to <= from) return cudaSuccess;
   tc::k_fill_pad4<<<(unsigned)((to - from + 255) / 256), 256, 0, st>>>(a, from, to);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_fill_pairs(float4* a, int64_t count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  tc::k_fill_pairs<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(a, count);
   return cudaGetLastError();
 }
 

@@ -101,3 +101,51 @@ def test_tc_checkpoint_resume_bitwise():
     assert np.array_equal(ea["nu"], eb["nu"]) and np.array_equal(ea["theta"], eb["theta"])
     a.close()
     b.close()
+
+
+def test_tc_iteration_matches_oracle_at_4096():
+    """Many tiles per CTA and a full grid: one bf16 iteration from the same oracle state
+    and the evaluation of log Z, against the oracle on the rounded points."""
+    w = W.highdim(n=4096, seed=13)
+    wr = rounded(w)
+    C, s, K = oracle_cost(wr)
+    P = O.LampParams(K=K)
+    st0 = O.lamp_run(C, wr.r, wr.c, P, 3)
+    sol, _, _ = gpu_solver(w, K=K, scale=s, prec="bf16_tc", check_every=1)
+    sol.set_state(st0.nu, st0.theta, st0.kappa, st0.t)
+    sol.iterate(1)
+    K_, tau1, tau2 = O.resolve_params(C, P)
+    ref1, info = O.lamp_step(C, wr.r, wr.c, K_, tau1, tau2, 0.0, O.calpha_of(wr.c, 0.01), 1.1, st0)
+    assert_pot_close(sol.get_state(), ref1, what="tc 4096 step")
+    sol.set_state(ref1.nu, ref1.theta, ref1.kappa, ref1.t)
+    obj = sol.objective()
+    rep = O.objective_report(C, wr.r, wr.c, K, 0.0, ref1)
+    assert_logZ_close(sol.get_state()["logZ"], rep["logZ"], what="tc 4096 logZ")
+    assert abs(obj["cost"] - rep["cost"]) <= 1e-6 * abs(rep["cost"])
+    sol.close()
+
+
+def test_tc_solve_4096_converges_like_fp32():
+    """At a size with many tiles per CTA both precisions reach 1e-6 in about the same
+    number of iterations (they solve nearly the same problem)."""
+    w = W.highdim(n=4096, seed=3)
+    its = {}
+    for prec in ("fp32", "bf16_tc"):
+        s, C, K = gpu_solver(w, prec=prec, tol=1e-6, max_iter=20000, check_every=50)
+        r = s.solve(allow_not_converged=False)
+        its[prec] = r["iters"]
+        s.close()
+    assert abs(its["bf16_tc"] - its["fp32"]) <= 0.1 * its["fp32"], its
+
+
+def test_tc_run_is_deterministic_across_graph_lengths():
+    """The same bf16 problem iterated with different device-loop lengths gives bit-identical
+    potentials (no race in the pipelined kernels; many tiles per CTA at n = 8192)."""
+    w = W.highdim(n=8192, seed=21)
+    out = []
+    for ce in (50, 7):
+        s, C, K = gpu_solver(w, prec="bf16_tc", check_every=ce)
+        s.iterate(400)
+        out.append(s.get_state())
+        s.close()
+    assert np.array_equal(out[0]["nu"], out[1]["nu"]) and np.array_equal(out[0]["theta"], out[1]["theta"])
