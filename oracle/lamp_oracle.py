@@ -48,6 +48,7 @@ __all__ = [
     "sinkhorn_log", "eot_value", "ot_lp", "ot_bruteforce_uniform",
     "grad_envelope", "D_Ha", "KL", "Dt_summand",
     "logZ_rows", "col_entries", "marginals_from_state",
+    "sqeuclid_cost_expanded", "lamp_step_streamed", "streamed_sup_norm",
 ]
 
 
@@ -68,6 +69,20 @@ def sqeuclid_cost(x: np.ndarray, y: np.ndarray, scale: float = 1.0, chunk: int =
     if scale != 1.0:
         out *= scale
     return out
+
+
+def sqeuclid_cost_expanded(x: np.ndarray, y: np.ndarray, scale: float = 1.0) -> np.ndarray:
+    """The same C_ij = scale |x_i - y_j|^2 in float64 written as |x_i|^2 + |y_j|^2 - 2 x_i . y_j
+    (a matrix product), for row blocks of large high-dimensional clouds where the
+    explicit differences would need n m d memory.  Agrees with sqeuclid_cost to
+    float64 rounding (pinned by a test)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    C = (x * x).sum(axis=1)[:, None] + (y * y).sum(axis=1)[None, :] - 2.0 * (x @ y.T)
+    np.maximum(C, 0.0, out=C)
+    if scale != 1.0:
+        C *= scale
+    return C
 
 
 def sup_norm(C: np.ndarray) -> float:
@@ -564,6 +579,36 @@ def col_entries(cost_rows: Callable[[np.ndarray], np.ndarray], n: int, cols: np.
         S = -kappa * (Cr[:, cols] + 2.0 * K * nu[None, cols])
         out += (r[rows, None] * np.exp(S - lz[:, None])).sum(axis=0)
     return out, logZ
+
+
+def streamed_sup_norm(cost_rows: Callable[[np.ndarray], np.ndarray], n: int, chunk: int = 512) -> float:
+    """||C||_inf over row blocks of a cost too large to hold (Section 2)."""
+    K = 0.0
+    for a in range(0, n, chunk):
+        K = max(K, float(np.abs(cost_rows(np.arange(a, min(n, a + chunk)))).max()))
+    return K
+
+
+def lamp_step_streamed(cost_rows: Callable[[np.ndarray], np.ndarray], n: int, r, c, K, tau1, tau2, eta, calpha,
+                       beta, state: LampState, chunk: int = 512):
+    """One iteration of Alg. 2 with C streamed in row blocks (O(chunk * m) memory):
+    the same steps as lamp_step, with the two marginals (Section 4.1) accumulated
+    block by block.  Returns (new_state, (A, B, logZ_A, logZ_B))."""
+    m = c.shape[0]
+    kap = state.kappa
+    nu = state.nu
+    theta = state.theta
+    kap1 = kappa_next(kap, eta, tau1)
+    w = tau1 / kap1
+    nubar = nu + w * (theta - nu)
+    cols = np.arange(m)
+    A, logZ_A = col_entries(cost_rows, n, cols, K, kap, nu, r, chunk)
+    thetabar = dual_mirror_map(theta, A, c, calpha, tau2, K)
+    nu_new = nu + w * (thetabar - nu)
+    B, logZ_B = col_entries(cost_rows, n, cols, K, kap1, nubar, r, chunk)
+    thetahat = dual_mirror_map(theta, B, c, calpha, tau2, K)
+    theta_new = tclip(thetahat, beta)
+    return LampState(state.t + 1, kap1, nu_new, theta_new), (A, B, logZ_A, logZ_B)
 
 
 def marginals_from_state(C, r, K, kappa, nu):

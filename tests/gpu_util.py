@@ -58,6 +58,17 @@ def gpu_solver(w, K=None, scale=None, **params):
     return L.Lamp(r, c, x=dev(w.x), y=dev(w.y), cost_scale=s if scale is None else scale, K=K, **params), C, K
 
 
+def gpu_solver_raw(w, K, scale=1.0, **params):
+    """The GPU context for workload w with an explicit K and cost scale, without
+    materialising the oracle's dense cost (for the full-size point clouds)."""
+    import paper_2511_11359_gb300 as L
+
+    r, c = dev(w.r), dev(w.c)
+    if w.kind == "dense":
+        return L.Lamp(r, c, C=dev(w.C), K=K, **params)
+    return L.Lamp(r, c, x=dev(w.x), y=dev(w.y), cost_scale=scale, K=K, **params)
+
+
 def assert_pot_close(st, ref, tol=POT_TOL, what=""):
     dn = np.abs(st["nu"] - ref.nu).max()
     dt = np.abs(st["theta"] - ref.theta).max()

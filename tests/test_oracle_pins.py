@@ -448,3 +448,25 @@ def test_solve_eta_positive_waits_for_kappa():
     eta, tol = 0.05, 1e-6
     st, info, conv = O.lamp_solve(C, r, c, O.LampParams(eta=eta), tol, 200000)
     assert conv and 1.0 - st.kappa * eta <= tol and info.res <= tol
+
+
+def test_expanded_cost_matches_differences():
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal((40, 64)).astype(np.float32)
+    y = (rng.standard_normal((33, 64)) + 0.5).astype(np.float32)
+    assert np.max(np.abs(O.sqeuclid_cost_expanded(x, y) - O.sqeuclid_cost(x, y))) < 1e-10
+
+
+def test_streamed_step_equals_dense_step():
+    """lamp_step_streamed (row blocks of C) reproduces lamp_step (dense C)."""
+    C, r, c = small_points(70, 45, seed=19)
+    P = O.LampParams()
+    K, tau1, tau2 = O.resolve_params(C, P)
+    ca = O.calpha_of(c, P.alpha)
+    st = O.lamp_run(C, r, c, P, 37)
+    ref, info = O.lamp_step(C, r, c, K, tau1, tau2, 0.0, ca, P.beta, st)
+    got, (A, B, lzA, lzB) = O.lamp_step_streamed(lambda rows: C[rows], 70, r, c, K, tau1, tau2, 0.0, ca, P.beta, st,
+                                                chunk=16)
+    assert np.max(np.abs(got.nu - ref.nu)) < 1e-13 and np.max(np.abs(got.theta - ref.theta)) < 1e-12
+    assert np.max(np.abs(A - info.A)) < 1e-15 and np.max(np.abs(lzB - info.logZ_B)) < 1e-12
+    assert O.streamed_sup_norm(lambda rows: C[rows], 70, chunk=9) == K
