@@ -143,8 +143,9 @@ def test_plain_2d_full_solve_and_certificate():
     st, info, conv = O.lamp_solve(C, w.r, w.c, O.LampParams(K=K), tol, 200000)
     assert conv and res["converged"] and res["infeas"] <= tol
     ot = O.ot_lp(C, w.r, w.c)
-    # <C, X> of an infeasible X can be below OT*; the certificate bounds the rounded plan:
-    # <C, Round(X)> <= <C, X> + 2K ||col - c||_1 <= OT* + 4K res + 2K log m / t
+    # the proof of Prop. infeas_bound (a) (App. D) bounds <C, X^t> - OT* <= 2K ||col - c||_1
+    # + 2K log m / t, i.e. cost + 2K res <= OT* + certificate; and Round(X^t) is feasible
+    # with ||X - Round(X)||_1 <= 2 res, so cost >= OT* - 2K res
     assert obj["cost"] + 2 * K * obj["col_res"] <= ot + obj["certificate"] + 1e-9
     assert obj["cost"] >= ot - 2 * K * obj["col_res"] - 1e-9
     assert abs(res["iters"] - st.t) <= max(2, 0.05 * st.t)
