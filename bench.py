@@ -333,14 +333,27 @@ def run_gpu(args, rank, world):
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                 "what": "stored C bytes of the " + ("row" if dom == 0 else "column") + " sweep"}
-    elif args.prec == "bf16_tc":
+    elif args.prec == "bf16_tc" or w.d <= 8:
+        # tensor-core sweeps, and the packed f32x2 direct-form sweeps (d <= 8): two ex2 per entry
         rate = L.measure_ex2_rate()
         peak = sms * rate * mhz * 1e6 / 1e12
         achieved = n * m * 2 / (kern_ms[dom] / 1e3) / 1e12
+        form = "tcgen05 x.y" if args.prec == "bf16_tc" else "f32x2 direct |x - y|^2"
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tex2/s", "frac": achieved / peak,
                 "traffic": None,
-                "what": "MUFU ex2 of the " + ("row" if dom == 0 else "column") + " sweep (2 ex2 per entry: streams A, B)",
+                "what": "MUFU ex2 of the " + ("row" if dom == 0 else "column") + f" sweep ({form}; 2 ex2 per entry: "
+                        "streams A, B)",
                 "peak_source": f"{sms} SMs x {rate:.2f} ex2/clk/SM (measured, lamp_measure_ex2_rate) x {mhz:.0f} MHz"}
+        if args.prec != "bf16_tc":
+            # float32 lane operations per entry of a regular iteration: d sub + d mul/fma (cost);
+            # stream A add + 2 fma (compensated exponent) + fma (weighted sum); stream B, through
+            # the shared row shift, add + fma + fma
+            lanes = 2 * w.d + 7
+            fpeak = sms * 128 * mhz * 1e6 / 1e12
+            fach = n * m * lanes / (kern_ms[dom] / 1e3) / 1e12
+            roof["fp32_pipe"] = {"lane_ops_per_entry": lanes, "achieved": fach, "peak": fpeak, "unit": "Tlane-op/s",
+                                 "frac": fach / fpeak,
+                                 "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz"}
     else:
         peak = sms * 128 * 2 * mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flop x max SM clock
         achieved = n * m * flops_per_entry / (kern_ms[dom] / 1e3) / 1e12

@@ -36,8 +36,9 @@ struct lamp_ctx {
   double* own_r = nullptr;
   double* own_c = nullptr;
   // graphs: [0] one iteration, [1] check_every iterations
-  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-  int64_t glen[2] = {0, 0};
+  // graph slots: 0 = one iteration, 1 = check_every iterations, 2 = one evaluation pass
+  cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
+  int64_t glen[3] = {0, 0, 0};
   DevState* host_dev = nullptr;  // pinned mirror for polling
   // LAMP_PREC_BF16_TC: bf16 copies (zero padded to 128-row multiples x 64 coordinates),
   // float32 copies of the rounded points, and their TMA descriptors
@@ -167,7 +168,7 @@ static int build_graph(lamp_ctx* ctx, int slot, int64_t len) {
   }
   CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
   for (int64_t i = 0; i < len; ++i) {
-    cudaError_t e = launch_iteration(ctx->in, ctx->k, ctx->w, ctx->g, ctx->prec, ctx->cap);
+    cudaError_t e = launch_iteration(ctx->in, ctx->k, ctx->w, ctx->g, ctx->prec, slot == 2, ctx->cap);
     if (e != cudaSuccess) {
       cudaGraph_t gg;
       cudaStreamEndCapture(ctx->cap, &gg);
@@ -253,6 +254,7 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
   k.kind = prob->kind;
   // direct-form cost (z = |x - y|^2) for small d; dot form x.y above
   k.zdot = (prob->kind == LAMP_COST_SQEUCLID && (prob->d > 8 || params->prec == LAMP_PREC_BF16_TC)) ? 1 : 0;
+  k.shared_shift = uses_direct_sweeps(k, params->prec) ? 1 : 0;
   k.eta = params->eta;
   k.alpha = params->alpha;
   k.clipb = std::tanh(params->beta / 2.0);
@@ -329,8 +331,8 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
   // workspace
   Work& w = ctx->w;
   const size_t n = (size_t)k.n, m = (size_t)k.m;
-  ctx->rowblocks = (int)((k.n + 255) / 256);
-  int colblocks = (int)((k.m + 255) / 256);
+  ctx->rowblocks = (int)fin_blocks(k.n);
+  int colblocks = (int)fin_blocks(k.m);
   size_t gradd = k.kind == LAMP_COST_SQEUCLID ? (size_t)std::min<int64_t>(std::max<int64_t>(k.d, 2), 8) : 2;
   // column / row data are padded to 128-entry multiples (padding entries contribute nothing)
   const size_t m_pad = (size_t)tc_pad(k.m), n_pad = (size_t)tc_pad(k.n);
@@ -341,7 +343,7 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
     if ((rc = dalloc(ctx, &w.rowshift[b], n))) return bail(rc);
   }
   if ((rc = dalloc(ctx, &w.g2row, n_pad))) return bail(rc);
-  if (ctx->prec == LAMP_PREC_BF16_TC) {
+  if (ctx->prec == LAMP_PREC_BF16_TC || k.shared_shift) {
     for (int b = 0; b < 2; ++b)
       if ((rc = dalloc(ctx, &w.colq2[b], m_pad))) return bail(rc);
     if ((rc = dalloc(ctx, &w.g2row2, n_pad))) return bail(rc);
@@ -545,6 +547,8 @@ static void fill_result(lamp_ctx* ctx, lamp_result* out) {
   out->status = d.status;
 }
 
+static int evaluate(lamp_ctx* ctx);
+
 extern "C" int lamp_solve(lamp_ctx* ctx, lamp_result* out) {
   if (!ctx) return fail(nullptr, LAMP_E_INVALID, "lamp_solve: null context");
   k_ctrl<<<1, 1, 0, ctx->stream>>>(ctx->w.dev, 0, ctx->params.tol, ctx->params.max_iter, -1, 0);
@@ -555,6 +559,12 @@ extern "C" int lamp_solve(lamp_ctx* ctx, lamp_result* out) {
     if (rc) return rc;
     if ((rc = poll(ctx))) return rc;
     if (ctx->host_dev->done) break;
+  }
+  if (ctx->k.shared_shift && ctx->host_dev->status == 0) {
+    // the regular iterations of the packed direct-form sweeps leave <C, X^t> out: one
+    // evaluation pass of the final state provides it
+    int rc = evaluate(ctx);
+    if (rc) return rc;
   }
   fill_result(ctx, out);
   const DevState& d = *ctx->host_dev;
@@ -598,7 +608,7 @@ extern "C" int lamp_iterate(lamp_ctx* ctx, int64_t iters) {
 static int evaluate(lamp_ctx* ctx) {
   k_ctrl<<<1, 1, 0, ctx->stream>>>(ctx->w.dev, 1, -1.0, 0, 0, 0);
   CK(cudaGetLastError());
-  int rc = run_graph(ctx, 0, 1);
+  int rc = run_graph(ctx, 2, 1);
   if (rc) return rc;
   return poll(ctx);
 }
@@ -674,8 +684,17 @@ extern "C" int lamp_set_state(lamp_ctx* ctx, const double* nu, const double* the
     for (int64_t i = 0; i < 2 * ctx->k.n; ++i)
       if (!std::isfinite(row_shifts[i])) return fail(ctx, LAMP_E_INVALID, "row_shifts must be finite");
     CK(launch_init_state(ctx->in, ctx->k, ctx->w, 0, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->w.rowshift[cur], row_shifts, ctx->k.n * sizeof(float2), cudaMemcpyHostToDevice,
-                       ctx->stream));
+    if (ctx->k.shared_shift) {
+      // both streams use stream A's shift: keep the pairs consistent whatever was passed
+      std::vector<float> rs(row_shifts, row_shifts + 2 * ctx->k.n);
+      for (int64_t i = 0; i < ctx->k.n; ++i) rs[2 * i + 1] = rs[2 * i];
+      CK(cudaMemcpyAsync(ctx->w.rowshift[cur], rs.data(), ctx->k.n * sizeof(float2), cudaMemcpyHostToDevice,
+                         ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+    } else {
+      CK(cudaMemcpyAsync(ctx->w.rowshift[cur], row_shifts, ctx->k.n * sizeof(float2), cudaMemcpyHostToDevice,
+                         ctx->stream));
+    }
   } else if ((rc = prime(ctx))) {
     return rc;
   }
@@ -726,7 +745,7 @@ extern "C" int lamp_time_kernels(lamp_ctx* ctx, int64_t iters, double* ms_out) {
   for (int64_t it = 0; it < iters && rc == LAMP_OK; ++it) {
     cudaEventRecord(ev[0], ctx->stream);
     for (int part = 0; part < 4; ++part) {
-      cudaError_t e = launch_iteration_part(ctx->in, ctx->k, ctx->w, ctx->g, ctx->prec, part, ctx->stream);
+      cudaError_t e = launch_iteration_part(ctx->in, ctx->k, ctx->w, ctx->g, ctx->prec, part, 0, ctx->stream);
       if (e != cudaSuccess) {
         rc = fail(ctx, LAMP_E_CUDA, "kernel launch: %s", cudaGetErrorString(e));
         break;
@@ -761,7 +780,7 @@ extern "C" const char* lamp_last_error(const lamp_ctx* ctx) { return ctx ? ctx->
 extern "C" void lamp_destroy(lamp_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  for (int s = 0; s < 2; ++s)
+  for (int s = 0; s < 3; ++s)
     if (ctx->gexec[s]) cudaGraphExecDestroy(ctx->gexec[s]);
   for (void* p : ctx->allocs) cudaFree(p);
   if (ctx->host_dev) cudaFreeHost(ctx->host_dev);

@@ -29,6 +29,13 @@
 // eta = 0 where kappa_t = t/(2K) grows without bound (Section 3.2).
 // The sub-grid remainder Br_j = Bcol_j - Bq_j enters as the factor
 // w_j = 2^{-Br_j} (row sums) or as a per-column factor after the sum (column sums).
+//
+// Shared row shift (packed direct-form sweeps, Consts::shared_shift): stream B
+// uses stream A's row shift, RqB_i = RqA_i, and its exponent is derived from
+// stream A's as v^B = (a^B - a^A) z + (v^A + (BqA_j - BqB_j)).  BqA_j - BqB_j is
+// a difference of two grid multiples, hence exact, and O(1): kappa_{t+1} nubar_j
+// and kappa_t nu_j differ by O(tau1), so v^B - v^A = O(1) for every entry and
+// the row sums of stream B stay within a few powers of two of 1.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -41,6 +48,11 @@ constexpr double kLn2 = 0.69314718055994530942;
 
 enum CostKind : int { COST_DENSE = 0, COST_SQEUCLID = 1 };
 
+// threads per block of the O(n + m) finalize kernels (float64 math: more, smaller
+// blocks spread it over more SMs); rowred / colred hold one partial per block
+constexpr int kFinThreads = 128;
+inline int64_t fin_blocks(int64_t len) { return (len + kFinThreads - 1) / kFinThreads; }
+
 // Problem constants, fixed for the lifetime of a context (passed by value).
 struct Consts {
   int64_t n, m;
@@ -52,7 +64,7 @@ struct Consts {
   double W;          // bound factor for the exponent offsets: |Bq|+|Rq| <= lambda*W + 128
   double rnx;        // sum_i r_i s |x_i|^2 (dot-form cost bookkeeping), 0 otherwise
   int32_t zdot;      // 1: z = x.y (dot form), 0: z = C/s (direct form)
-  int32_t pad;
+  int32_t shared_shift;  // 1: both streams use stream A's row shift (packed direct-form sweeps)
 };
 
 // Parameters of one iteration's sweeps, derived from kappa_t alone.
@@ -111,10 +123,12 @@ __host__ __device__ inline SweepParams make_sweep_params(double kap, const Const
 
 // round-to-nearest multiple of the power-of-two grid g, exact in float64
 __host__ __device__ inline double quantize(double x, double g) {
+  // g is a power of two, so x * (1 / g) == x / g exactly (and avoids a float64 division)
+  const double ginv = 1.0 / g;
 #ifdef __CUDA_ARCH__
-  return rint(x / g) * g;
+  return rint(x * ginv) * g;
 #else
-  return __builtin_rint(x / g) * g;
+  return __builtin_rint(x * ginv) * g;
 #endif
 }
 
@@ -135,6 +149,44 @@ __device__ __forceinline__ float ex2(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
+}
+
+// packed pairs of floats (fma / add / sub / mul .rn.f32x2: two IEEE round-to-nearest
+// operations per instruction, lane by lane identical to the scalar ones)
+__device__ __forceinline__ uint64_t pk(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 upk(uint64_t v) {
+  float2 f;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(f.x), "=f"(f.y) : "l"(v));
+  return f;
+}
+__device__ __forceinline__ uint64_t f2fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2add(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2sub(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// 2^v for a pair of entries: v = al z + (ah z + o), o = -(Rq + Bq) exact (see the top of this file)
+__device__ __forceinline__ uint64_t exp2_pair(uint64_t ah2, uint64_t al2, uint64_t z2, uint64_t o2) {
+  const float2 v = upk(f2fma(al2, z2, f2fma(ah2, z2, o2)));
+  return pk(ex2(v.x), ex2(v.y));
 }
 
 // Knuth's branch-free TwoSum: s + e == a + b exactly
@@ -183,7 +235,7 @@ struct Work {
   float4* g2row;       // per row {RqA, qA, RqB, qB} for the column sweep
   // the same data in the packed-pair layout read by the tensor-core sweeps (null when
   // unused): for entries 2p, 2p+1 two float4, [2p] = {-offA_2p, -offA_2p+1, wgtA_2p,
-  // wgtA_2p+1} and [2p+1] = the same for stream B; padding halves hold {-inf, 0}
+  // wgtA_2p+1} and [2p+1] = the same for stream B; padding halves hold {-2^100, 0}
   float4* colq2[2];
   float4* g2row2;
   double* rowpart;     // [splits_rows][2][n] partial row sums
@@ -227,8 +279,10 @@ cudaError_t launch_check_marginals(const Inputs& in, const Consts& k, const Work
 cudaError_t launch_init_state(const Inputs& in, const Consts& k, const Work& w, int zero, cudaStream_t st);
 cudaError_t launch_prime(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
                          cudaStream_t st);
+// eval = 1: an evaluation pass, whose column sweep also accumulates <C, X^t> (the
+// packed direct-form column sweep leaves it out of the regular iterations)
 cudaError_t launch_iteration(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
-                             cudaStream_t st);
+                             int eval, cudaStream_t st);
 void prepare_kernels();
 // tcgen05 path (lamp_tc.cu)
 size_t tc_smem_bytes();
@@ -242,7 +296,7 @@ int tc_blocks_per_sm(int which);
 cudaError_t tc_launch_sweep(bool rows, const void* map_x, const void* map_y, const Work& w, const Consts& k,
                             int splits, cudaStream_t st);
 cudaError_t launch_iteration_part(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
-                                  int part, cudaStream_t st);
+                                  int part, int eval, cudaStream_t st);
 int tile_outer_cols(const Consts& k, int prec);
 int tile_inner_cols(const Consts& k, int prec);
 cudaError_t launch_grad(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
@@ -253,5 +307,7 @@ void set_last_error_null(const char* msg);
 int sweep_blocks_per_sm(const Consts& k, int prec, int which);
 int tile_outer(const Consts& k, int prec);
 int tile_inner(const Consts& k, int prec);
+// whether the packed direct-form sweeps serve this problem (then Consts::shared_shift = 1)
+bool uses_direct_sweeps(const Consts& k, int prec);
 
 }  // namespace lamp

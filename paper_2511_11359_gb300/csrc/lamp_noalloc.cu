@@ -185,8 +185,8 @@ extern "C" int lamp_marginals_noalloc(const lamp_problem* prob, double K, double
   w.colpart = cv.take<double>((size_t)g.cols_split * 3 * m);
   w.nx = cv.take<double>(n);
   w.ny = cv.take<double>(m);
-  w.rowred = cv.take<double>((n + 255) / 256);
-  w.colred = cv.take<double>(3 * ((m + 255) / 256));
+  w.rowred = cv.take<double>((size_t)fin_blocks(k.n));
+  w.colred = cv.take<double>(3 * (size_t)fin_blocks(k.m));
   w.rowmax = cv.take<float>((size_t)g.rows_split * 2 * n);
   w.scratch = cv.take<double>(1);
   w.dev = cv.take<DevState>(1);
@@ -213,7 +213,7 @@ extern "C" int lamp_marginals_noalloc(const lamp_problem* prob, double K, double
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = launch_init_state(in, k, w, 0, st);
   if (e == cudaSuccess) e = launch_prime(in, k, w, g, LAMP_PREC_FP32, st);
-  if (e == cudaSuccess) e = launch_iteration(in, k, w, g, LAMP_PREC_FP32, st);
+  if (e == cudaSuccess) e = launch_iteration(in, k, w, g, LAMP_PREC_FP32, 1, st);
   if (e == cudaSuccess && cost_out) {
     k_noalloc_out<<<1, 1, 0, st>>>(w.dev, cost_out);
     e = cudaGetLastError();

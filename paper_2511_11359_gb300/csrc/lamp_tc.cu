@@ -180,39 +180,6 @@ __device__ __forceinline__ void tmem_ld32_wait(uint32_t taddr, uint32_t (&v)[32]
 
 
 
-// packed pairs of floats (fma / add / mul .rn.f32x2: two IEEE round-to-nearest
-// operations per instruction, lane by lane identical to the scalar ones)
-__device__ __forceinline__ uint64_t pk(float lo, float hi) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ float2 upk(uint64_t v) {
-  float2 f;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(f.x), "=f"(f.y) : "l"(v));
-  return f;
-}
-__device__ __forceinline__ uint64_t f2fma(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ uint64_t f2add(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ uint64_t f2mul(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-// 2^v for a pair of entries: v = al z + (ah z + o), o = -(Rq + Bq) exact (see lamp_common.cuh)
-__device__ __forceinline__ uint64_t exp2_pair(uint64_t ah2, uint64_t al2, uint64_t z2, uint64_t o2) {
-  const float2 v = upk(f2fma(al2, z2, f2fma(ah2, z2, o2)));
-  return pk(ex2(v.x), ex2(v.y));
-}
-
 // barrier over the epilogue threads (named barrier 1) returning the OR of `v`
 // across them, so that every epilogue warp takes the same branch
 __device__ __forceinline__ bool epi_bar_or(bool v) {
@@ -489,10 +456,12 @@ __global__ void k_fill_pad4(float4* __restrict__ a, int64_t from, int64_t to) {
   if (i < to) a[i] = make_float4(INFINITY, 0.f, INFINITY, 0.f);
 }
 
-// packed-pair arrays: every half starts as padding {-off = -inf, wgt = 0}
+// packed-pair arrays: every half starts as padding {-off = -2^100, wgt = 0}
 __global__ void k_fill_pairs(float4* __restrict__ a, int64_t count) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < count) a[i] = make_float4(-INFINITY, -INFINITY, 0.f, 0.f);
+  // padding: a finite offset far below any real one (differences of two padding offsets,
+  // which the direct-form sweeps take, stay 0 instead of inf - inf), zero weight
+  if (i < count) a[i] = make_float4(-0x1p100f, -0x1p100f, 0.f, 0.f);
 }
 
 }  // namespace tc
