@@ -158,9 +158,31 @@ LAMP_API int lamp_iterate(lamp_ctx* ctx, int64_t iters);
  *   out[3] H(X^t)               (entropy identity of App. D, from O(n+m) values)
  *   out[4] P^eta(X^t)           (Eq. prob:l1_ot_primal)
  *   out[5] certificate RHS 4K||col-c||_1 + 2K log m / t (Prop. infeas_bound (a); eta = 0, t >= 1, else NaN)
- *   out[6] saddle dual max(D(theta^t), D(nu^t)) (App. B; NaN: not computed by this build)
+ *   out[6] saddle dual max(D(theta^t), D(nu^t)), as lamp_dual (two or four extra sweeps)
  *   out[7] K */
 LAMP_API int lamp_objective(lamp_ctx* ctx, double out[8]);
+
+/* Dual function of the saddle problem (App. B, Eqs. def:dual_spp, def:dual_spp_e)
+ *   D(phi)     = sum_i r_i min_j (C_ij + 2K phi_j) - 2K <c, phi>                       (eta = 0)
+ *   D^eta(phi) = sum_i r_i softmin^eta_j (C_ij + 2K phi_j) - 2K <c, phi> - eta H(r)     (eta > 0)
+ * at phi = theta^t (out[0]) and phi = nu^t (out[1]); host memory, synchronises.  For
+ * any phi in [-1, 1]^m it is a lower bound on the optimal value of the penalised problem
+ * (weak duality).  eta = 0: one row-max sweep per phi, evaluated in float32 with
+ * offsets on the kernels' grid (absolute error about 1e-6 K); eta > 0: a row-max and a
+ * row-sum sweep per phi at kappa = 1/eta.  The state is not changed. */
+LAMP_API int lamp_dual(lamp_ctx* ctx, double out[2]);
+
+/* Round (Alg. 3, Altschuler et al.) of the current X^t, returned in factored form
+ *   Round(X^t) = X^t diag(y) + delta_r delta_c^T / ||delta_r||_1,
+ * with y_j = min(c_j / col(X^t)_j, 1), delta_c = c - col(X^t diag(y)) = max(c - col(X^t), 0)
+ * and delta_r = r - row(X^t diag(y)) >= 0 (Step 1 is the identity: row(X^t) = r by
+ * construction).  Round(X^t) is in Pi(r, c).  out (host, synchronises):
+ *   out[0] <C, Round(X^t)>   (the left side of Prop. infeas_bound (a) plus <C, X*>)
+ *   out[1] ||delta_r||_1      out[2] ||delta_c||_1      out[3] <C, X^t diag(y)>
+ * y (m), delta_r (n), delta_c (m): device float64 buffers, each may be NULL.
+ * Cost: one evaluation pass, one row sweep and O(n + m) work (|x - y|^2), or one more
+ * pass over the stored C (LAMP_COST_DENSE).  The state is not changed. */
+LAMP_API int lamp_round(lamp_ctx* ctx, double out[4], double* y, double* delta_r, double* delta_c);
 
 /* Gradient of L = <C, X> - eta H(X) at the current state's X^t with respect
  * to the points (envelope theorem): dL/dx_i = sum_j X_ij dC_ij/dx_i and

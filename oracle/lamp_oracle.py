@@ -43,7 +43,7 @@ __all__ = [
     "dual_mirror_map", "tclip", "calpha_of", "resolve_params",
     "lamp_initial_state", "lamp_step", "lamp_run", "lamp_solve",
     "lamp_performant_run", "pdmp_run", "primal_mirror_map",
-    "round_plan", "entropy", "penalized_objective", "entropy_from_normalizers",
+    "round_plan", "round_factors", "entropy", "penalized_objective", "entropy_from_normalizers",
     "saddle_dual", "certificate_rhs", "objective_report",
     "sinkhorn_log", "eot_value", "ot_lp", "ot_bruteforce_uniform",
     "grad_envelope", "D_Ha", "KL", "Dt_summand",
@@ -370,15 +370,24 @@ def pdmp_run(C, r, c, params: LampParams, T: int, record=None):
 # Round, objectives, duals, certificate
 
 
-def round_plan(X: np.ndarray, r: np.ndarray, c: np.ndarray) -> np.ndarray:
-    """Alg. 3 (Round, Altschuler et al.), steps 1-4.  With ||delta_r||_1 = 0 the
-    rank-one correction is skipped (X'' is already feasible up to rounding)."""
+def round_factors(X: np.ndarray, r: np.ndarray, c: np.ndarray):
+    """Alg. 3 (Round, Altschuler et al.), steps 1-3: the row scaling x, the column
+    scaling y, X'' = diag(x) X diag(y), and delta_r = r - row(X''),
+    delta_c = c - col(X'').  Returns (x, y, X'', delta_r, delta_c)."""
     x = np.minimum(r / X.sum(axis=1), 1.0)
     X1 = x[:, None] * X
     y = np.minimum(c / X1.sum(axis=0), 1.0)
     X2 = X1 * y[None, :]
     dr = r - X2.sum(axis=1)
     dc = c - X2.sum(axis=0)
+    return x, y, X2, dr, dc
+
+
+def round_plan(X: np.ndarray, r: np.ndarray, c: np.ndarray) -> np.ndarray:
+    """Alg. 3 (Round), step 4 on the factors of round_factors: X'' plus the rank-one
+    correction delta_r delta_c^T / ||delta_r||_1.  With ||delta_r||_1 = 0 the
+    correction is skipped (X'' is already feasible up to rounding)."""
+    _, _, X2, dr, dc = round_factors(X, r, c)
     l1 = np.abs(dr).sum()
     if l1 == 0.0:
         return X2

@@ -12,7 +12,9 @@ Entry points mirror include/lamp.h:
     Lamp(...)              lamp_create            (device tensors, borrowed)
     Lamp.solve()           lamp_solve             (run Alg. 2 to the tolerance)
     Lamp.iterate(k)        lamp_iterate           (exactly k iterations)
-    Lamp.objective()       lamp_objective         (<C,X>, residuals, H, P^eta, certificate, K)
+    Lamp.objective()       lamp_objective         (<C,X>, residuals, H, P^eta, certificate, dual, K)
+    Lamp.dual()            lamp_dual              (saddle dual D at theta^t and nu^t)
+    Lamp.round()           lamp_round             (Round(X^t) in factored form, its cost)
     Lamp.grad()            lamp_grad              (envelope gradient w.r.t. the points)
     Lamp.get_state()/set_state()                  (checkpoint / restore of the O(n+m) state)
     LampHost(...)          lamp_create_owned / lamp_step_host (host buffers)
@@ -51,7 +53,7 @@ EXPORTED_SYMBOLS = [
     "lamp_params_default", "lamp_create", "lamp_solve", "lamp_iterate", "lamp_objective", "lamp_grad",
     "lamp_get_state", "lamp_set_state", "lamp_step_host", "lamp_create_owned",
     "lamp_launches_per_iteration", "lamp_last_error", "lamp_destroy", "lamp_time_kernels",
-    "lamp_marginals_noalloc", "lamp_measure_ex2_rate",
+    "lamp_marginals_noalloc", "lamp_measure_ex2_rate", "lamp_round", "lamp_dual",
 ]
 
 library_path = Path(__file__).resolve().parent / "liblamp.so"
@@ -98,6 +100,8 @@ def _load():
     L.lamp_iterate.argtypes = [vp, i64]
     L.lamp_objective.argtypes = [vp, ctypes.POINTER(dbl)]
     L.lamp_grad.argtypes = [vp, vp, vp]
+    L.lamp_round.argtypes = [vp, ctypes.POINTER(dbl), vp, vp, vp]
+    L.lamp_dual.argtypes = [vp, ctypes.POINTER(dbl)]
     L.lamp_get_state.argtypes = [vp, vp, vp, vp, ctypes.POINTER(dbl), ctypes.POINTER(i64), vp]
     L.lamp_set_state.argtypes = [vp, vp, vp, dbl, i64, vp]
     L.lamp_step_host.argtypes = [vp, vp, vp, vp, vp, i64, ctypes.POINTER(dbl), vp]
@@ -249,6 +253,31 @@ class Lamp:
         _check(_get_lib().lamp_objective(self._h, out), self._h)
         keys = ["cost", "col_res", "row_res", "entropy", "P_eta", "certificate", "dual", "K"]
         return dict(zip(keys, list(out)))
+
+    def dual(self) -> dict:
+        """D(theta^t), D(nu^t): the saddle-problem dual at both potentials (App. B)."""
+        out = (ctypes.c_double * 2)()
+        _check(_get_lib().lamp_dual(self._h, out), self._h)
+        return {"theta": out[0], "nu": out[1]}
+
+    def round(self, want_vectors: bool = False) -> dict:
+        """Round(X^t) = X^t diag(y) + dr dc^T / ||dr||_1 (Alg. 3): its cost and, with
+        want_vectors, the device float64 tensors y (m), dr (n), dc (m)."""
+        import torch
+
+        dev = torch.device("cuda", torch.cuda.current_device())
+        vec = {}
+        if want_vectors:
+            vec = {"y": torch.empty(self.m, dtype=torch.float64, device=dev),
+                   "dr": torch.empty(self.n, dtype=torch.float64, device=dev),
+                   "dc": torch.empty(self.m, dtype=torch.float64, device=dev)}
+        out = (ctypes.c_double * 4)()
+        _check(_get_lib().lamp_round(self._h, out, ctypes.c_void_p(_ptr(vec.get("y"))),
+                                     ctypes.c_void_p(_ptr(vec.get("dr"))), ctypes.c_void_p(_ptr(vec.get("dc")))),
+               self._h)
+        res = {"cost": out[0], "dr_l1": out[1], "dc_l1": out[2], "cost_scaled": out[3]}
+        res.update(vec)
+        return res
 
     def grad(self, want_x: bool = True, want_y: bool = True):
         import torch

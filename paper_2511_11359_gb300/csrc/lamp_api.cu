@@ -35,7 +35,6 @@ struct lamp_ctx {
   float* own_b = nullptr;  // y
   double* own_r = nullptr;
   double* own_c = nullptr;
-  // graphs: [0] one iteration, [1] check_every iterations
   // graph slots: 0 = one iteration, 1 = check_every iterations, 2 = one evaluation pass
   cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
   int64_t glen[3] = {0, 0, 0};
@@ -193,6 +192,8 @@ __global__ void k_ctrl(DevState* dev, int eval_only, double tol, long long tmax_
   dev->ticket = 0u;
   if (set) dev->status = 0;
 }
+
+__global__ void k_mark_done(DevState* dev) { dev->done = 1; }
 
 __global__ void k_set_state(DevState* dev, long long t, double kappa) {
   dev->t = t;
@@ -352,6 +353,8 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
   if ((rc = dalloc(ctx, &w.colpart, (size_t)g.cols_split * std::max<size_t>(3, gradd) * m))) return bail(rc);
   if ((rc = dalloc(ctx, &w.logZ, n))) return bail(rc);
   if ((rc = dalloc(ctx, &w.colA, m))) return bail(rc);
+  if ((rc = dalloc(ctx, &w.colz, m))) return bail(rc);
+  if ((rc = dalloc(ctx, &w.rscr, rscr_doubles(k.n, k.m, k.kind == LAMP_COST_SQEUCLID ? (int)k.d : 0)))) return bail(rc);
   if ((rc = dalloc(ctx, &w.nx, n))) return bail(rc);
   if ((rc = dalloc(ctx, &w.ny, m))) return bail(rc);
   if ((rc = dalloc(ctx, &w.rowred, (size_t)ctx->rowblocks))) return bail(rc);
@@ -613,6 +616,59 @@ static int evaluate(lamp_ctx* ctx) {
   return poll(ctx);
 }
 
+// run evaluation passes outside the iteration after an evaluate(): the sweeps return at
+// once while dev->done is set, so clear it for the passes and set it again after
+static int begin_passes(lamp_ctx* ctx) {
+  k_ctrl<<<1, 1, 0, ctx->stream>>>(ctx->w.dev, 1, -1.0, 0, 0, 0);
+  CK(cudaGetLastError());
+  return LAMP_OK;
+}
+static int end_passes(lamp_ctx* ctx) {
+  k_mark_done<<<1, 1, 0, ctx->stream>>>(ctx->w.dev);
+  CK(cudaGetLastError());
+  return LAMP_OK;
+}
+
+static int dual_values(lamp_ctx* ctx, double out[2]) {
+  // evaluate() or poll() has run: host_dev->cur is the state's parity
+  const int cur = ctx->host_dev->cur;
+  int rc = begin_passes(ctx);
+  if (rc) return rc;
+  for (int which = 0; which < 2; ++which)
+    CK(launch_dual(ctx->in, ctx->k, ctx->w, ctx->g, ctx->prec, cur, which, ctx->w.scratch + 4 + 2 * which,
+                   ctx->stream));
+  if ((rc = end_passes(ctx))) return rc;
+  double h[4];
+  CK(cudaMemcpyAsync(h, ctx->w.scratch + 4, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const Consts& k = ctx->k;
+  // D(phi) = sum_i r_i rowmin_i - 2K <c, phi>  (eta > 0: softmin, and the constant -eta H(r))
+  for (int which = 0; which < 2; ++which)
+    out[which] = h[2 * which] - 2.0 * k.K * h[2 * which + 1] - (k.eta > 0.0 ? k.eta * ctx->Hr : 0.0);
+  return LAMP_OK;
+}
+
+extern "C" int lamp_dual(lamp_ctx* ctx, double out[2]) {
+  if (!ctx || !out) return fail(ctx, LAMP_E_INVALID, "lamp_dual: null argument");
+  int rc = poll(ctx);
+  if (rc) return rc;
+  return dual_values(ctx, out);
+}
+
+extern "C" int lamp_round(lamp_ctx* ctx, double out[4], double* y, double* delta_r, double* delta_c) {
+  if (!ctx || !out) return fail(ctx, LAMP_E_INVALID, "lamp_round: null argument");
+  int rc = evaluate(ctx);
+  if (rc) return rc;
+  const int cur = ctx->host_dev->cur;
+  if ((rc = begin_passes(ctx))) return rc;
+  CK(launch_round(ctx->in, ctx->k, ctx->w, ctx->g, ctx->prec, cur, ctx->w.scratch, y, delta_r, delta_c,
+                  ctx->stream));
+  if ((rc = end_passes(ctx))) return rc;
+  CK(cudaMemcpyAsync(out, ctx->w.scratch, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return LAMP_OK;
+}
+
 extern "C" int lamp_objective(lamp_ctx* ctx, double out[8]) {
   if (!ctx || !out) return fail(ctx, LAMP_E_INVALID, "lamp_objective: null argument");
   int rc = evaluate(ctx);
@@ -627,10 +683,13 @@ extern "C" int lamp_objective(lamp_ctx* ctx, double out[8]) {
   out[3] = H;
   out[4] = d.costA + 2.0 * k.K * d.res - k.eta * H;
   out[5] = (k.eta == 0.0 && d.t >= 1) ? 4.0 * k.K * d.res + 2.0 * k.K * ctx->log_m / (double)d.t : NAN;
-  out[6] = NAN;
   out[7] = k.K;
   if (d.status == LAMP_E_TIMEOUT) return fail(ctx, LAMP_E_TIMEOUT, "a device-side wait ran out of its budget");
   if (d.status != 0) return fail(ctx, LAMP_E_NUMERIC, "non-finite or out-of-range sum");
+  // the dual bound at theta^t and nu^t (the larger is reported)
+  double D2[2];
+  if ((rc = dual_values(ctx, D2))) return rc;
+  out[6] = std::max(D2[0], D2[1]);
   return LAMP_OK;
 }
 

@@ -52,6 +52,11 @@ enum CostKind : int { COST_DENSE = 0, COST_SQEUCLID = 1 };
 // blocks spread it over more SMs); rowred / colred hold one partial per block
 constexpr int kFinThreads = 128;
 inline int64_t fin_blocks(int64_t len) { return (len + kFinThreads - 1) / kFinThreads; }
+// doubles of Work::rscr: per-block partials of up to 4 + d fields for rows and columns,
+// the reduced fields and the results
+inline size_t rscr_doubles(int64_t n, int64_t m, int d) {
+  return (size_t)(fin_blocks(n) + fin_blocks(m) + 2) * (size_t)(4 + d) + 256;
+}
 
 // Problem constants, fixed for the lifetime of a context (passed by value).
 struct Consts {
@@ -65,6 +70,12 @@ struct Consts {
   double rnx;        // sum_i r_i s |x_i|^2 (dot-form cost bookkeeping), 0 otherwise
   int32_t zdot;      // 1: z = x.y (dot form), 0: z = C/s (direct form)
   int32_t shared_shift;  // 1: both streams use stream A's row shift (packed direct-form sweeps)
+  // evaluation passes outside the iteration (rounding, dual bound) run the sweeps on
+  // scratch column data with these set: kap_ovr >= 0 replaces kappa_t, and
+  // same_kappa = 1 gives stream B stream A's kappa (two weightings of one exponent)
+  double kap_ovr = -1.0;
+  int32_t same_kappa = 0;
+  int32_t pad = 0;
 };
 
 // Parameters of one iteration's sweeps, derived from kappa_t alone.
@@ -94,10 +105,15 @@ __host__ __device__ inline double pow2i(int e) {
   return r;
 }
 
+// kappa of the sweeps: the state's, unless an evaluation pass overrides it
+__host__ __device__ inline double sweep_kappa(double dev_kappa, const Consts& k) {
+  return k.kap_ovr >= 0.0 ? k.kap_ovr : dev_kappa;
+}
+
 __host__ __device__ inline SweepParams make_sweep_params(double kap, const Consts& k) {
   SweepParams p;
   p.kapA = kap;
-  p.kapB = kappa_next(kap, k);
+  p.kapB = k.same_kappa ? kap : kappa_next(kap, k);
   p.lamA = p.kapA * kLog2e;
   p.lamB = p.kapB * kLog2e;
   if (!k.zdot) {
@@ -189,6 +205,17 @@ __device__ __forceinline__ uint64_t exp2_pair(uint64_t ah2, uint64_t al2, uint64
   return pk(ex2(v.x), ex2(v.y));
 }
 
+// the column data {BqA, wA, BqB, wB} of one column for sweep parameters sp: Bcol of
+// each stream rounded to the grid, and the factor 2^{-remainder}
+__device__ __forceinline__ float4 column_data(double nu_j, double nubar_j, double sny_j, const SweepParams& sp,
+                                              const Consts& k) {
+  double bA = sp.lamA * (sny_j + 2.0 * k.K * nu_j);
+  double bB = sp.lamB * (sny_j + 2.0 * k.K * nubar_j);
+  double qA = quantize(bA, sp.g);
+  double qB = quantize(bB, sp.g);
+  return make_float4((float)qA, (float)exp2(-(bA - qA)), (float)qB, (float)exp2(-(bB - qB)));
+}
+
 // Knuth's branch-free TwoSum: s + e == a + b exactly
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
@@ -242,6 +269,9 @@ struct Work {
   double* colpart;     // [splits_cols][3][m] partial column sums (A, B, cost-weighted A)
   double* logZ;        // [n] natural-log normalisers of X^t
   double* colA;        // [m] col(X^t)
+  double* colz;        // [m] sum_i C_ij X_ij of the last pass that accumulated the cost, without
+                       // the dot form's sum_i s|x_i|^2 X_ij (added by its users)
+  double* rscr;        // reduction scratch of the rounding / dual-bound passes
   double* nx;          // [n] |x_i|^2 (SQEUCLID)
   double* ny;          // [m] |y_j|^2 (SQEUCLID)
   double* rowred;      // [rowfin blocks] partial <r, log Z>
@@ -301,6 +331,14 @@ int tile_outer_cols(const Consts& k, int prec);
 int tile_inner_cols(const Consts& k, int prec);
 cudaError_t launch_grad(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
                         float* dx, float* dy, cudaStream_t st);
+// evaluation passes (lamp_eval.cu); `cur` is the state-buffer parity, read by the host beforehand.
+// Round: out4 (device, 4 doubles) = {<C, Round(X^t)>, ||delta_r||_1, ||delta_c||_1, <C, X''>}
+cudaError_t launch_round(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec, int cur,
+                         double* out4, double* y, double* dr, double* dc, cudaStream_t st);
+// dual bound at theta^t (which = 0) or nu^t (which = 1): out2 (device) = {sum_i r_i rowmin_i,
+// <c, phi>}, with rowmin the row min (eta = 0) or row softmin (eta > 0) of C_ij + 2K phi_j
+cudaError_t launch_dual(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec, int cur,
+                        int which, double* out2, cudaStream_t st);
 int launches_per_iteration(const Consts& k, int prec);
 // record a message for lamp_last_error(NULL) (errors raised without a context)
 void set_last_error_null(const char* msg);

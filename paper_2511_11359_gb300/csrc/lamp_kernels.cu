@@ -83,7 +83,7 @@ k_pts_sweep(const float* __restrict__ P_out, const float* __restrict__ P_in, int
   int64_t it1 = it0 + tiles_per_split;
   if (it1 > ntiles_in) it1 = ntiles_in;
 
-  SweepParams sp = make_sweep_params(dev->kappa, k);
+  SweepParams sp = make_sweep_params(sweep_kappa(dev->kappa, k), k);
 
   for (int idx = tid; idx < d * kPT; idx += kThreads) {
     int p = idx / d, kk = idx - p * d;
@@ -383,7 +383,7 @@ k_pts_direct(const float* __restrict__ P_out, const float* __restrict__ P_in, in
     }
   }
 
-  const SweepParams sp = make_sweep_params(dev->kappa, k);
+  const SweepParams sp = make_sweep_params(sweep_kappa(dev->kappa, k), k);
   const uint64_t ahA2 = pk(sp.ahA, sp.ahA), alA2 = pk(sp.alA, sp.alA);
   const float dal = (float)(sp.aB - sp.aA);  // a^B - a^A
   const uint64_t da2 = pk(dal, dal);
@@ -522,7 +522,7 @@ k_dense_rows(const float* __restrict__ C, int64_t ldc, int64_t n, int64_t m, con
   const int64_t c0 = (int64_t)split * chunks_per_split;
   int64_t c1 = c0 + chunks_per_split;
   if (c1 > nchunks) c1 = nchunks;
-  SweepParams sp = make_sweep_params(dev->kappa, k);
+  SweepParams sp = make_sweep_params(sweep_kappa(dev->kappa, k), k);
   const float ahA = sp.ahA, alA = sp.alA, ahB = sp.ahB, alB = sp.alB;
 
   float oA[kDR], oB[kDR];
@@ -637,7 +637,7 @@ k_dense_cols(const float* __restrict__ C, int64_t ldc, int64_t n, int64_t m, con
   const int64_t i0 = (int64_t)split * rows_per_split;
   int64_t i1 = i0 + rows_per_split;
   if (i1 > n) i1 = n;
-  SweepParams sp = make_sweep_params(dev->kappa, k);
+  SweepParams sp = make_sweep_params(sweep_kappa(dev->kappa, k), k);
   const float ahA = sp.ahA, alA = sp.alA, ahB = sp.ahB, alB = sp.alB;
 
   float oA[4], oB[4];
@@ -774,16 +774,6 @@ __global__ void k_vec_stats(const double* __restrict__ v, int64_t len, double* o
   }
 }
 
-// the column data {BqA, wA, BqB, wB} of one column for sweep parameters sp
-__device__ __forceinline__ float4 column_data(double nu_j, double nubar_j, double sny_j, const SweepParams& sp,
-                                              const Consts& k) {
-  double bA = sp.lamA * (sny_j + 2.0 * k.K * nu_j);
-  double bB = sp.lamB * (sny_j + 2.0 * k.K * nubar_j);
-  double qA = quantize(bA, sp.g);
-  double qB = quantize(bB, sp.g);
-  return make_float4((float)qA, (float)exp2(-(bA - qA)), (float)qB, (float)exp2(-(bB - qB)));
-}
-
 // set the column data of the current state buffer from its (nu, theta) and dev->kappa
 __global__ void k_init_cols(const Work w, const Consts k, int zero) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -795,7 +785,7 @@ __global__ void k_init_cols(const Work w, const Consts k, int zero) {
   double* __restrict__ theta = w.theta[cur];
   float4* __restrict__ colq = w.colq[cur];
   if (zero) { nu[j] = 0.0; theta[j] = 0.0; }
-  SweepParams sp = make_sweep_params(dev->kappa, k);
+  SweepParams sp = make_sweep_params(sweep_kappa(dev->kappa, k), k);
   double wt = k.tau1 / sp.kapB;  // tau1 eta_{t+1}
   double nb = nu[j] + wt * (theta[j] - nu[j]);
   double sny = k.zdot ? k.s * ny[j] : 0.0;
@@ -811,7 +801,7 @@ __global__ void k_prime_fin(const Work w, int splits, const Consts k) {
   const DevState* __restrict__ dev = w.dev;
   const float* __restrict__ pmax = w.rowmax;
   float2* __restrict__ rowshift = w.rowshift[dev->cur];
-  SweepParams sp = make_sweep_params(dev->kappa, k);
+  SweepParams sp = make_sweep_params(sweep_kappa(dev->kappa, k), k);
   float mA = -INFINITY, mB = -INFINITY;
   for (int s = 0; s < splits; ++s) {
     mA = fmaxf(mA, pmax[((int64_t)s * 2 + 0) * k.n + i]);
@@ -928,6 +918,7 @@ k_col_fin(const Work w, int splits, const double* __restrict__ cvec, int rowbloc
     res = fabs(A - cj);
     cnu = A * nuj;
     colA[j] = A;
+    if (with_cost && w.colz) w.colz[j] = cost;
     if (!eval_only) {
       const double ca = cj + k.alpha / (double)k.m;  // c^alpha (Section 3.1)
       const double gj = 2.0 * k.tau2 * k.K / ca;

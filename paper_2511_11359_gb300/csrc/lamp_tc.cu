@@ -338,7 +338,7 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
     // ---------------- epilogue: warps 0-7; lane index t, column half h ----------------
     const int t = (warp & 3) * 32 + lane;  // TMEM lane = row of D owned (0..127)
     const int h = warp >> 2;               // which 64 of the 128 accumulator columns
-    const SweepParams sp = make_sweep_params(dev->kappa, k);
+    const SweepParams sp = make_sweep_params(sweep_kappa(dev->kappa, k), k);
     const uint64_t ahA2 = pk(sp.ahA, sp.ahA), alA2 = pk(sp.alA, sp.alA);
     const uint64_t ahB2 = pk(sp.ahB, sp.ahB), alB2 = pk(sp.alB, sp.alB);
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;  // TMEM lane field

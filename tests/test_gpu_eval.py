@@ -1,0 +1,146 @@
+"""lamp_round (Alg. 3) and lamp_dual (App. B, Eqs. def:dual_spp / def:dual_spp_e) through
+the C ABI against the FP64 oracle.
+
+The GPU context is put on the oracle's own state at iteration T (lamp_set_state with
+the oracle's nu, theta, kappa), so both sides evaluate the same X^T; the oracle rounds
+the dense X^T (round_factors / round_plan) and evaluates saddle_dual densely."""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from tests.gpu_util import OBJ_TOL, RES_FLOOR, gpu_solver, oracle_cost
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # (name, kind, n, m, d, eta, prec, T): direct-form and dot-form float32 sweeps, the
+    # tcgen05 path on bf16-rounded points, stored costs; ragged sizes spanning several
+    # CTAs and inner splits
+    ("pts2", "points", 300, 257, 2, 0.0, "fp32", 40),
+    ("pts3_eta", "points", 1500, 1100, 3, 0.05, "fp32", 25),
+    ("dense", "dense", 290, 1100, 0, 0.0, "fp32", 30),
+    ("dense_eta", "dense", 700, 300, 0, 0.02, "fp32", 20),
+    ("dot16", "points", 400, 300, 16, 0.0, "fp32", 30),
+    ("tc64", "points", 384, 300, 64, 0.0, "bf16_tc", 30),
+]
+
+
+def _problem(case):
+    name, kind, n, m, d, eta, prec, T = case
+    seed = sum(name.encode()) % 991
+    if kind == "dense":
+        return W.dense_problem(name, n, m, seed=seed, eta=eta)
+    dist = "gauss_shift" if d > 8 else "uniform"
+    w = W.points_problem(name, n, m, d, seed=seed, dist=dist, marg="random", cost_scale=1.0, eta=eta)
+    if prec == "bf16_tc":
+        w = dataclasses.replace(w, x=W.bf16_round(w.x), y=W.bf16_round(w.y))
+    return w
+
+
+def _setup(case):
+    name, kind, n, m, d, eta, prec, T = case
+    w = _problem(case)
+    C, s, K = oracle_cost(w)
+    st = O.lamp_run(C, w.r, w.c, O.LampParams(eta=eta, K=K), T)
+    sol, _, _ = gpu_solver(w, K=K, scale=s, eta=eta, prec=prec, check_every=5)
+    sol.set_state(st.nu, st.theta, st.kappa, st.t)
+    return w, C, s, K, st, sol
+
+
+def _dot_slack(w, s):
+    """float32 error of an on-the-fly cost in the dot form (d > 8, or bf16 inputs):
+    d accumulated roundings of terms of size up to s (|x|^2 + |y|^2)."""
+    if w.kind == "dense" or w.d <= 8:
+        return 0.0
+    nx = (np.asarray(w.x, np.float64) ** 2).sum(1).max()
+    ny = (np.asarray(w.y, np.float64) ** 2).sum(1).max()
+    return w.d * 2.0 ** -24 * s * (nx + ny)
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_round_matches_oracle(case):
+    w, C, s, K, st, sol = _setup(case)
+    g = sol.round(want_vectors=True)
+    X = w.r[:, None] * O.dual_to_primal(C, K, st.kappa, st.nu)[0]
+    x, y, X2, dr, dc = O.round_factors(X, w.r, w.c)
+    assert np.abs(x - 1.0).max() <= 1e-12  # row(X^t) = r: Step 1 is the identity
+    Xr = O.round_plan(X, w.r, w.c)
+    ref_cost = float((C * Xr).sum())
+    ref_cpp = float((C * X2).sum())
+    slack = _dot_slack(w, s)
+    gy, gdr, gdc = (g[k].cpu().numpy() for k in ("y", "dr", "dc"))
+    assert np.abs(gy - y).max() <= 1e-5, np.abs(gy - y).max()
+    assert np.all(np.abs(gdc - dc) <= 1e-5 * w.c + 1e-9)
+    assert np.abs(gdr - dr).sum() <= 1e-5 * np.abs(dr).sum() + RES_FLOOR
+    assert np.all(gdr >= 0.0) and np.all(gdc >= 0.0)
+    assert abs(g["dr_l1"] - np.abs(dr).sum()) <= 1e-5 * np.abs(dr).sum() + RES_FLOOR
+    assert abs(g["dc_l1"] - np.abs(dc).sum()) <= 1e-5 * np.abs(dc).sum() + RES_FLOOR
+    # mass balance: sum delta_r = sum delta_c = 1 - mass(X'')
+    assert abs(g["dr_l1"] - g["dc_l1"]) <= 2 * RES_FLOOR
+    assert abs(g["cost_scaled"] - ref_cpp) <= OBJ_TOL * abs(ref_cpp) + slack
+    assert abs(g["cost"] - ref_cost) <= OBJ_TOL * abs(ref_cost) + 4 * K * RES_FLOOR + slack
+    # the factored plan is feasible: col = y * col(X^t) + delta_c = c (checked on the oracle's col)
+    colX = X.sum(axis=0)
+    assert np.abs(gy * colX + gdc - w.c).max() <= 2e-5 * w.c.max()
+    sol.close()
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_dual_matches_oracle(case):
+    name, kind, n, m, d, eta, prec, T = case
+    w, C, s, K, st, sol = _setup(case)
+    D = sol.dual()
+    ref_t = O.saddle_dual(C, w.r, w.c, K, st.theta, eta)
+    ref_n = O.saddle_dual(C, w.r, w.c, K, st.nu, eta)
+    # eta = 0: the row minimum from float32 row maxima with offsets on the kernels' grid
+    # (|error| about 1e-6 K); eta > 0: the row sums at kappa = 1/eta
+    tol = 2e-6 * K + 4 * _dot_slack(w, s)
+    assert abs(D["theta"] - ref_t) <= tol, (D["theta"], ref_t)
+    assert abs(D["nu"] - ref_n) <= tol, (D["nu"], ref_n)
+    obj = sol.objective()
+    assert obj["dual"] == max(D["theta"], D["nu"])
+    sol.close()
+
+
+def test_round_dual_and_certificate_bracket_the_lp_optimum():
+    """eta = 0 on an LP-sized problem after T iterations: weak duality D(theta^T) <= OT*
+    (App. B), Round(X^T) is feasible so <C, Round(X^T)> >= OT*, and Prop. infeas_bound (a)
+    bounds <C, Round(X^T)> - OT* by the certificate 4K ||col - c||_1 + 2K log m / T."""
+    w = W.points_problem("lpbracket", 40, 36, 2, seed=5, dist="uniform", marg="random", cost_scale=1.0)
+    C, s, K = oracle_cost(w)
+    ot = O.ot_lp(C, w.r, w.c)
+    sol, _, _ = gpu_solver(w, K=K, scale=s, check_every=10)
+    for T in (20, 200):
+        sol.iterate(T - (0 if T == 20 else 20))
+        obj = sol.objective()
+        rd = sol.round()
+        D = sol.dual()
+        assert max(D["theta"], D["nu"]) <= ot + 2e-6 * K
+        assert rd["cost"] >= ot - OBJ_TOL * ot
+        assert rd["cost"] - ot <= obj["certificate"] + OBJ_TOL * ot
+        assert obj["certificate"] == pytest.approx(4 * K * obj["col_res"] + 2 * K * math.log(w.m) / T, rel=1e-12)
+    sol.close()
+
+
+def test_round_leaves_the_state_alone():
+    """lamp_round and lamp_dual use only scratch buffers: the trajectory after them is the
+    trajectory without them, bit for bit."""
+    w = W.points_problem("roundstate", 257, 300, 3, seed=11, dist="uniform", marg="random", cost_scale=1.0)
+    C, s, K = oracle_cost(w)
+    a, _, _ = gpu_solver(w, K=K, scale=s, check_every=4)
+    b, _, _ = gpu_solver(w, K=K, scale=s, check_every=4)
+    a.iterate(13)
+    b.iterate(13)
+    b.round(want_vectors=True)
+    b.dual()
+    a.iterate(9)
+    b.iterate(9)
+    sa, sb = a.get_state(), b.get_state()
+    assert np.array_equal(sa["nu"], sb["nu"]) and np.array_equal(sa["theta"], sb["theta"])
+    assert np.array_equal(sa["row_shifts"], sb["row_shifts"])
+    a.close()
+    b.close()
