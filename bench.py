@@ -34,6 +34,22 @@ METRIC = "cost-entries/s/iter and time-to-infeasibility≤1e-6 at n=m=2^15 (BF16
 UNIT = "cost-entries/s"
 
 
+def job_throughput(units_per_rank: float, local_seconds: float, dist=None, device=None):
+    """Whole-job throughput of weak-scaled replicas: every rank processed
+    `units_per_rank` units in its own timed region; the job took the slowest rank's
+    time.  Returns (units of all ranks / max seconds, max seconds).  `dist` is
+    torch.distributed (any backend) or None for one process."""
+    import torch
+
+    t = torch.tensor([float(local_seconds)], dtype=torch.float64, device=device)
+    world = 1
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        world = dist.get_world_size()
+    sec = float(t.item())
+    return world * float(units_per_rank) / sec, sec
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -248,11 +264,8 @@ def run_gpu(args, rank, world):
     # per-kernel device times, measured with events between the launches
     kern_ms = solver.time_kernels(max(3, min(args.steps, 10)))
     clocks = sampler.stop()
-    t_dev = torch.tensor([total_ms], dtype=torch.float64, device=devc)
-    if dist:
-        dist.all_reduce(t_dev, op=dist.ReduceOp.MAX)
-    total_ms = float(t_dev.item())
-    value = world * n * m * args.steps / (total_ms / 1e3)
+    value, total_s = job_throughput(n * m * args.steps, total_ms / 1e3, dist, devc)
+    total_ms = total_s * 1e3
 
     # end to end through the C ABI with host buffers: every step uploads the inputs
     # from pinned host memory, runs one iteration and reads back nu and the residual
@@ -274,7 +287,8 @@ def run_gpu(args, rank, world):
             hst.step(1, a_h, b_h, r_h, c_h, nu_out=nu_h)
         el = time.perf_counter() - t0
         hst.close()
-        e2e = {"value": world * n * m * args.e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d_bytes),
+        e2e_value, _ = job_throughput(n * m * args.e2e_steps, el, dist, devc)
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d_bytes),
                "d2h_bytes_per_step": int(8 + 8 * m), "steps": args.e2e_steps}
 
     info = {}

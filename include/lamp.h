@@ -232,6 +232,14 @@ LAMP_API int lamp_time_kernels(lamp_ctx* ctx, int64_t iters, double* ms_out);
  * frees two small device buffers; synchronises. */
 LAMP_API int lamp_measure_ex2_rate(double* ex2_per_clk_per_sm);
 
+/* Self-test of failure detection on the GPU: launches one thread that waits, with the
+ * bounded mbarrier wait of the tensor-core sweeps limited to `polls` polls (1..2^30), on
+ * a barrier that nothing arrives on.  The wait gives up, records LAMP_E_TIMEOUT in a
+ * device status word and the kernel returns normally; *status receives that word
+ * (LAMP_E_TIMEOUT expected).  Returns LAMP_OK, or LAMP_E_INVALID / LAMP_E_NOMEM /
+ * LAMP_E_CUDA.  The device stays usable afterwards.  Synchronises. */
+LAMP_API int lamp_selftest_wait_timeout(int64_t polls, int* status);
+
 /* Number of kernel launches one iteration issues (for launch accounting). */
 LAMP_API int64_t lamp_launches_per_iteration(const lamp_ctx* ctx);
 

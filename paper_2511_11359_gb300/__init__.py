@@ -33,7 +33,7 @@ __all__ = [
     "LampError", "Lamp", "LampHost", "LampOT", "lamp_ot_loss", "lib", "library_path",
     "LAMP_OK", "LAMP_E_INVALID", "LAMP_E_CUDA", "LAMP_E_NOMEM", "LAMP_E_NOT_CONVERGED",
     "LAMP_E_NUMERIC", "LAMP_E_TIMEOUT", "LAMP_E_UNSUPPORTED",
-    "COST_DENSE", "COST_SQEUCLID", "PREC_FP32", "PREC_BF16_TC", "EXPORTED_SYMBOLS",
+    "COST_DENSE", "COST_SQEUCLID", "PREC_FP32", "PREC_BF16_TC", "EXPORTED_SYMBOLS", "selftest_wait_timeout",
 ]
 
 LAMP_OK = 0
@@ -53,7 +53,7 @@ EXPORTED_SYMBOLS = [
     "lamp_params_default", "lamp_create", "lamp_solve", "lamp_iterate", "lamp_objective", "lamp_grad",
     "lamp_get_state", "lamp_set_state", "lamp_step_host", "lamp_create_owned",
     "lamp_launches_per_iteration", "lamp_last_error", "lamp_destroy", "lamp_time_kernels",
-    "lamp_marginals_noalloc", "lamp_measure_ex2_rate", "lamp_round", "lamp_dual",
+    "lamp_marginals_noalloc", "lamp_measure_ex2_rate", "lamp_round", "lamp_dual", "lamp_selftest_wait_timeout",
 ]
 
 library_path = Path(__file__).resolve().parent / "liblamp.so"
@@ -101,6 +101,7 @@ def _load():
     L.lamp_objective.argtypes = [vp, ctypes.POINTER(dbl)]
     L.lamp_grad.argtypes = [vp, vp, vp]
     L.lamp_round.argtypes = [vp, ctypes.POINTER(dbl), vp, vp, vp]
+    L.lamp_selftest_wait_timeout.argtypes = [i64, ctypes.POINTER(ctypes.c_int)]
     L.lamp_dual.argtypes = [vp, ctypes.POINTER(dbl)]
     L.lamp_get_state.argtypes = [vp, vp, vp, vp, ctypes.POINTER(dbl), ctypes.POINTER(i64), vp]
     L.lamp_set_state.argtypes = [vp, vp, vp, dbl, i64, vp]
@@ -161,6 +162,14 @@ def measure_ex2_rate() -> float:
     L.lamp_measure_ex2_rate.argtypes = [ctypes.POINTER(ctypes.c_double)]
     _check(L.lamp_measure_ex2_rate(ctypes.byref(v)))
     return v.value
+
+
+def selftest_wait_timeout(polls: int) -> int:
+    """Run the bounded-wait self-test (lamp_selftest_wait_timeout) and return the device
+    status word it produced (LAMP_E_TIMEOUT when the wait gave up as designed)."""
+    st = ctypes.c_int(0)
+    _check(_get_lib().lamp_selftest_wait_timeout(int(polls), ctypes.byref(st)))
+    return st.value
 
 
 def _ptr(t) -> int:

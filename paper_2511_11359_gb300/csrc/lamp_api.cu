@@ -834,6 +834,14 @@ extern "C" int64_t lamp_launches_per_iteration(const lamp_ctx* ctx) {
   return launches_per_iteration(ctx->k, ctx->prec);
 }
 
+extern "C" int lamp_selftest_wait_timeout(int64_t polls, int* status) {
+  if (!status || polls < 1 || polls > (int64_t)1 << 30)
+    return fail(nullptr, LAMP_E_INVALID, "lamp_selftest_wait_timeout: status must be non-NULL, 1 <= polls <= 2^30");
+  int rc = tc_wait_selftest((uint32_t)polls, status);
+  if (rc) return fail(nullptr, rc, "lamp_selftest_wait_timeout: CUDA error");
+  return LAMP_OK;
+}
+
 extern "C" const char* lamp_last_error(const lamp_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
 
 extern "C" void lamp_destroy(lamp_ctx* ctx) {

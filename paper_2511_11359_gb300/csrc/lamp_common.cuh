@@ -322,6 +322,8 @@ cudaError_t tc_fill_pads(float4* a, int64_t from, int64_t to, cudaStream_t st);
 cudaError_t tc_fill_pairs(float4* a, int64_t count, cudaStream_t st);
 cudaError_t tc_make_map(void* map_out, const void* base, int64_t rows_pad);
 cudaError_t tc_prepare();
+// self-test of the bounded mbarrier wait (0, or a LAMP_E_* code); *status = the device status word
+int tc_wait_selftest(uint32_t polls, int* status);
 int tc_blocks_per_sm(int which);
 cudaError_t tc_launch_sweep(bool rows, const void* map_x, const void* map_y, const Work& w, const Consts& k,
                             int splits, cudaStream_t st);

@@ -89,8 +89,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // bounded wait; false when the CTA is in error or the limit ran out (then the error is recorded)
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, Bars* B, DevState* dev) {
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, Bars* B, DevState* dev,
+                                          uint32_t limit = kWaitLimit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*(volatile int*)&B->err) return false;
   }
@@ -464,7 +465,40 @@ __global__ void k_fill_pairs(float4* __restrict__ a, int64_t count) {
   if (i < count) a[i] = make_float4(-0x1p100f, -0x1p100f, 0.f, 0.f);
 }
 
+// Self-test of the bounded wait: one thread waits on a barrier that nothing arrives on
+// (phase 0 of a fresh barrier with one expected arrival); after `limit` polls the wait
+// gives up, records LAMP_E_TIMEOUT in dev->status and the kernel returns normally.
+__global__ void k_wait_selftest(uint32_t limit, DevState* dev) {
+  __shared__ __align__(8) Bars B;
+  if (threadIdx.x == 0) {
+    mbar_init(&B.full[0], 1);
+    B.err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const bool ok = mbar_wait(&B.full[0], 0, &B, dev, limit);
+    if (ok) atomicExch(&dev->status, -1);  // impossible: nothing arrives
+  }
+}
+
 }  // namespace tc
+
+int tc_wait_selftest(uint32_t polls, int* status) {
+  DevState* d = nullptr;
+  if (cudaMalloc(&d, sizeof(DevState)) != cudaSuccess) return 3;
+  cudaError_t e = cudaMemset(d, 0, sizeof(DevState));
+  if (e == cudaSuccess) {
+    tc::k_wait_selftest<<<1, 32>>>(polls, d);
+    e = cudaGetLastError();
+  }
+  DevState h{};
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(DevState), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return 2;
+  *status = h.status;
+  return 0;
+}
 
 size_t tc_smem_bytes() {
   // alignment slack + fixed tile + ring + barriers + packed pairs (2 x 128 float4)

@@ -84,6 +84,17 @@ def test_null_context_calls(L):
     assert L.lib.lamp_create(None, None, None, None) == L.LAMP_E_INVALID
 
 
+def test_evaluation_entry_points_validate_on_host(L):
+    out = (ctypes.c_double * 4)()
+    assert L.lib.lamp_round(None, out, None, None, None) == L.LAMP_E_INVALID
+    assert L.lib.lamp_dual(None, out) == L.LAMP_E_INVALID
+    st = ctypes.c_int(0)
+    assert L.lib.lamp_selftest_wait_timeout(0, ctypes.byref(st)) == L.LAMP_E_INVALID
+    assert L.lib.lamp_selftest_wait_timeout(1 << 31, ctypes.byref(st)) == L.LAMP_E_INVALID
+    assert L.lib.lamp_selftest_wait_timeout(10, None) == L.LAMP_E_INVALID
+    assert b"polls" in L.lib.lamp_last_error(None)
+
+
 def test_struct_layouts_match_header(L, tmp_path):
     """The binding's ctypes structures mirror include/lamp.h: compare every field
     offset and the struct sizes with a C program compiled against the header."""

@@ -44,7 +44,8 @@ MUTANTS = [
     ("col_r", "(r[:, None] * p).sum(axis=0)", "(r[:, None] * p).sum(axis=1)",
      PINS.test_lamp_equals_explicit_pdmp, (16, 16, 2, 0.0)),
     ("tclip", "np.tanh(beta / 2.0)", "np.tanh(beta)", PINS.test_tclip_bounds, ()),
-    ("round_plan", "X2 = X1 * y[None, :]", "X2 = X1", PINS.test_round_is_feasible_and_within_bound, (0,)),
+    ("round_factors", "X2 = X1 * y[None, :]", "X2 = X1", PINS.test_round_is_feasible_and_within_bound, (0,)),
+    ("round_plan", "np.outer(dr, dc) / l1", "np.outer(dc, dr).T / l1 * 0.5", PINS.test_round_is_feasible_and_within_bound, (0,)),
     ("entropy_from_normalizers", "2.0 * K * kappa", "K * kappa", PINS.test_entropy_identity, (0.0,)),
     ("saddle_dual", "- 2.0 * K * (c @ theta)", "+ 2.0 * K * (c @ theta)",
      PINS.test_saddle_dual_strong_duality_at_lp_potentials, ()),
