@@ -162,6 +162,16 @@ LAMP_API int lamp_iterate(lamp_ctx* ctx, int64_t iters);
  *   out[7] K */
 LAMP_API int lamp_objective(lamp_ctx* ctx, double out[8]);
 
+/* Transport-map application (App. E, colour transfer): with the current
+ * X^t = diag(r) p^{eta_t}(nu^t) and p row-stochastic,
+ *   side 0: out = p V      (V: device m x k float32 row-major; out: device n x k)
+ *   side 1: out = p^T U    (U: device n x k float32 row-major; out: device m x k)
+ * 1 <= k <= 8 value columns (colour channels, coordinates: p y is the barycentric map).
+ * One evaluation pass, then one recompute sweep of X^t over all n m entries with
+ * float32 exponents as in the iteration and float64 accumulation across tiles.
+ * Asynchronous on the context's stream after the evaluation pass. */
+LAMP_API int lamp_apply_map(lamp_ctx* ctx, const float* V, int64_t k, float* out, int side);
+
 /* Dual function of the saddle problem (App. B, Eqs. def:dual_spp, def:dual_spp_e)
  *   D(phi)     = sum_i r_i min_j (C_ij + 2K phi_j) - 2K <c, phi>                       (eta = 0)
  *   D^eta(phi) = sum_i r_i softmin^eta_j (C_ij + 2K phi_j) - 2K <c, phi> - eta H(r)     (eta > 0)

@@ -15,6 +15,7 @@ Entry points mirror include/lamp.h:
     Lamp.objective()       lamp_objective         (<C,X>, residuals, H, P^eta, certificate, dual, K)
     Lamp.dual()            lamp_dual              (saddle dual D at theta^t and nu^t)
     Lamp.round()           lamp_round             (Round(X^t) in factored form, its cost)
+    Lamp.apply_map(V, side) lamp_apply_map        (p V or p^T U: transport-map application)
     Lamp.grad()            lamp_grad              (envelope gradient w.r.t. the points)
     Lamp.get_state()/set_state()                  (checkpoint / restore of the O(n+m) state)
     LampHost(...)          lamp_create_owned / lamp_step_host (host buffers)
@@ -54,6 +55,7 @@ EXPORTED_SYMBOLS = [
     "lamp_get_state", "lamp_set_state", "lamp_step_host", "lamp_create_owned",
     "lamp_launches_per_iteration", "lamp_last_error", "lamp_destroy", "lamp_time_kernels",
     "lamp_marginals_noalloc", "lamp_measure_ex2_rate", "lamp_round", "lamp_dual", "lamp_selftest_wait_timeout",
+    "lamp_apply_map",
 ]
 
 library_path = Path(__file__).resolve().parent / "liblamp.so"
@@ -103,6 +105,7 @@ def _load():
     L.lamp_round.argtypes = [vp, ctypes.POINTER(dbl), vp, vp, vp]
     L.lamp_selftest_wait_timeout.argtypes = [i64, ctypes.POINTER(ctypes.c_int)]
     L.lamp_dual.argtypes = [vp, ctypes.POINTER(dbl)]
+    L.lamp_apply_map.argtypes = [vp, vp, i64, vp, ctypes.c_int]
     L.lamp_get_state.argtypes = [vp, vp, vp, vp, ctypes.POINTER(dbl), ctypes.POINTER(i64), vp]
     L.lamp_set_state.argtypes = [vp, vp, vp, dbl, i64, vp]
     L.lamp_step_host.argtypes = [vp, vp, vp, vp, vp, i64, ctypes.POINTER(dbl), vp]
@@ -268,6 +271,20 @@ class Lamp:
         out = (ctypes.c_double * 2)()
         _check(_get_lib().lamp_dual(self._h, out), self._h)
         return {"theta": out[0], "nu": out[1]}
+
+    def apply_map(self, V, side: int = 0):
+        """p V (side 0, V: m x k) or p^T U (side 1, U: n x k) for the current X^t = diag(r) p
+        (lamp_apply_map); V a device float32 tensor with 1 <= k <= 8 columns."""
+        import torch
+
+        V = V.contiguous()
+        if V.dim() == 1:
+            V = V[:, None]
+        rows = self.n if side == 0 else self.m
+        out = torch.empty((rows, V.shape[1]), dtype=torch.float32, device=V.device)
+        _check(_get_lib().lamp_apply_map(self._h, ctypes.c_void_p(_ptr(V)), int(V.shape[1]),
+                                         ctypes.c_void_p(_ptr(out)), int(side)), self._h)
+        return out
 
     def round(self, want_vectors: bool = False) -> dict:
         """Round(X^t) = X^t diag(y) + dr dc^T / ||dr||_1 (Alg. 3): its cost and, with

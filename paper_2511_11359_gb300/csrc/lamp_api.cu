@@ -334,7 +334,8 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
   const size_t n = (size_t)k.n, m = (size_t)k.m;
   ctx->rowblocks = (int)fin_blocks(k.n);
   int colblocks = (int)fin_blocks(k.m);
-  size_t gradd = k.kind == LAMP_COST_SQEUCLID ? (size_t)std::min<int64_t>(std::max<int64_t>(k.d, 2), 8) : 2;
+  // partial sums of the gradient (d values per point) and of the transport map (up to 8)
+  const size_t gradd = 8;
   // column / row data are padded to 128-entry multiples (padding entries contribute nothing)
   const size_t m_pad = (size_t)tc_pad(k.m), n_pad = (size_t)tc_pad(k.n);
   for (int b = 0; b < 2; ++b) {
@@ -626,6 +627,17 @@ static int begin_passes(lamp_ctx* ctx) {
 static int end_passes(lamp_ctx* ctx) {
   k_mark_done<<<1, 1, 0, ctx->stream>>>(ctx->w.dev);
   CK(cudaGetLastError());
+  return LAMP_OK;
+}
+
+extern "C" int lamp_apply_map(lamp_ctx* ctx, const float* V, int64_t k, float* out, int side) {
+  if (!ctx || !V || !out) return fail(ctx, LAMP_E_INVALID, "lamp_apply_map: null argument");
+  if (k < 1 || k > 8) return fail(ctx, LAMP_E_INVALID, "lamp_apply_map: 1 <= k <= 8 value columns (got %lld)",
+                                  (long long)k);
+  if (side != 0 && side != 1) return fail(ctx, LAMP_E_INVALID, "lamp_apply_map: side must be 0 (p V) or 1 (p^T U)");
+  int rc = evaluate(ctx);
+  if (rc) return rc;
+  CK(launch_map(ctx->in, ctx->k, ctx->w, ctx->g, ctx->host_dev->cur, V, (int)k, out, side, ctx->stream));
   return LAMP_OK;
 }
 

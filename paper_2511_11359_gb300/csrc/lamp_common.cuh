@@ -333,6 +333,9 @@ int tile_outer_cols(const Consts& k, int prec);
 int tile_inner_cols(const Consts& k, int prec);
 cudaError_t launch_grad(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
                         float* dx, float* dy, cudaStream_t st);
+// transport-map application (lamp_kernels.cu): out = p V (side 0) or p^T U (side 1), 1 <= dk <= 8
+cudaError_t launch_map(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int cur, const float* V,
+                       int dk, float* out, int side, cudaStream_t st);
 // evaluation passes (lamp_eval.cu); `cur` is the state-buffer parity, read by the host beforehand.
 // Round: out4 (device, 4 doubles) = {<C, Round(X^t)>, ||delta_r||_1, ||delta_c||_1, <C, X''>}
 cudaError_t launch_round(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec, int cur,

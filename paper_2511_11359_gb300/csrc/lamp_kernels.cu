@@ -58,11 +58,13 @@ struct SweepIO {
   const float4* indat[2];
 };
 
+// M_GRAD accumulates sum_b 2^{v_ab} weight_b V_b[0:DG] with V = Vin (n_in x DG, row-major)
+// when given, else the inner points' own coordinates (the gradient, DG = d)
 template <int MODE, int DG, bool DIFF>
 __global__ void __launch_bounds__(kThreads, 1)
 k_pts_sweep(const float* __restrict__ P_out, const float* __restrict__ P_in, int64_t n_out, int64_t n_in, int d,
             const SweepIO io, double* __restrict__ part, float* __restrict__ pmax, int tiles_per_split,
-            const DevState* __restrict__ dev, const Consts k) {
+            const DevState* __restrict__ dev, const Consts k, const float* __restrict__ Vin) {
   if ((MODE == M_ROWSUM || MODE == M_COLSUM) && dev->done) return;
   const int cur = dev->cur;
   const float2* __restrict__ off2 = cur ? io.off2[1] : io.off2[0];
@@ -72,6 +74,7 @@ k_pts_sweep(const float* __restrict__ P_out, const float* __restrict__ P_in, int
   float* sOut = smem;                          // [d][128]
   float* sIn = smem + d * kPT;                 // [d][128]
   float4* sDat = reinterpret_cast<float4*>(smem + 2 * d * kPT);  // [128]
+  float* sV = smem + 2 * d * kPT + 4 * kPT;                        // [DG][128] (M_GRAD with Vin)
 
   const int tid = threadIdx.x;
   const int tx = tid & 15;
@@ -138,6 +141,13 @@ k_pts_sweep(const float* __restrict__ P_out, const float* __restrict__ P_in, int
       int p = idx / d, kk = idx - p * d;
       int64_t gi = i0 + p;
       sIn[kk * kPT + p] = gi < n_in ? P_in[gi * d + kk] : 0.0f;
+    }
+    if (MODE == M_GRAD && Vin) {
+      for (int idx = tid; idx < DG * kPT; idx += kThreads) {
+        int p = idx / (DG > 0 ? DG : 1), q = idx - p * (DG > 0 ? DG : 1);
+        int64_t gi = i0 + p;
+        sV[q * kPT + p] = gi < n_in ? Vin[gi * DG + q] : 0.0f;
+      }
     }
     if (tid < kPT) {
       int64_t gi = i0 + tid;
@@ -242,8 +252,9 @@ k_pts_sweep(const float* __restrict__ P_out, const float* __restrict__ P_in, int
           const float vA = __fmaf_rn(alA, zz, __fmaf_rn(ahA, zz, -(oA[a] + dat[b].x)));
           const float pA = ex2(vA) * dat[b].y;
           const int ib = (b < 4) ? (tx * 4 + b) : (64 + tx * 4 + b - 4);
+          const float* src = Vin ? sV : sIn;
 #pragma unroll
-          for (int q = 0; q < DG; ++q) g[q] = __fmaf_rn(pA, sIn[q * kPT + ib], g[q]);
+          for (int q = 0; q < DG; ++q) g[q] = __fmaf_rn(pA, src[q * kPT + ib], g[q]);
         }
 #pragma unroll
         for (int q = 0; q < DG; ++q) gacc[a][q] += (double)g[q];
@@ -1039,7 +1050,9 @@ __global__ void k_grad_fin_cols(const Work w, int splits, int64_t np, int d, con
 
 static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-static size_t pts_smem(int d) { return (size_t)(2 * d * kPT) * sizeof(float) + kPT * sizeof(float4); }
+static size_t pts_smem(int d, int dv = 0) {
+  return (size_t)(2 * d * kPT + dv * kPT) * sizeof(float) + kPT * sizeof(float4);
+}
 
 static SweepIO io_same(const float2* o2, const float4* o4, const float4* in) {
   SweepIO io;
@@ -1052,13 +1065,13 @@ static SweepIO io_same(const float2* o2, const float4* o4, const float4* in) {
 template <int MODE, int DG>
 static cudaError_t launch_pts(const float* Pout, const float* Pin, int64_t nout, int64_t nin, int d, const SweepIO& io,
                               double* part, float* pmax, int splits, const DevState* dev, const Consts& k,
-                              cudaStream_t st) {
+                              cudaStream_t st, const float* V = nullptr) {
   auto kern = k.zdot ? k_pts_sweep<MODE, DG, false> : k_pts_sweep<MODE, DG, true>;
-  size_t sm = pts_smem(d);
+  size_t sm = pts_smem(d, V ? DG : 0);
   int64_t tin = cdiv(nin, kPT);
   int tps = (int)cdiv(tin, splits);
   dim3 grid((unsigned)cdiv(nout, kPT), (unsigned)splits);
-  kern<<<grid, kThreads, sm, st>>>(Pout, Pin, nout, nin, d, io, part, pmax, tps, dev, k);
+  kern<<<grid, kThreads, sm, st>>>(Pout, Pin, nout, nin, d, io, part, pmax, tps, dev, k, V);
   return cudaGetLastError();
 }
 
@@ -1213,8 +1226,9 @@ int launches_per_iteration(const Consts& k, int prec) { return 4; }
 
 template <int MODE, int DG>
 static void set_attr() {
-  cudaFuncSetAttribute(k_pts_sweep<MODE, DG, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pts_smem(64));
-  cudaFuncSetAttribute(k_pts_sweep<MODE, DG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pts_smem(64));
+  const int sm = (int)pts_smem(64, DG);
+  cudaFuncSetAttribute(k_pts_sweep<MODE, DG, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_pts_sweep<MODE, DG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
 // raise the dynamic shared-memory limit of every sweep instantiation once, before any capture
@@ -1309,6 +1323,156 @@ cudaError_t launch_grad(const Inputs& in, const Consts& k, const Work& w, const 
     case 6: return launch_grad_d<6>(in, k, w, g, dx, dy, st);
     case 7: return launch_grad_d<7>(in, k, w, g, dx, dy, st);
     case 8: return launch_grad_d<8>(in, k, w, g, dx, dy, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// transport-map application (App. E, colour transfer): out = p V (side 0, V: m x k) or
+// out = p^T U (side 1, U: n x k) for the current X^t = diag(r) p, 1 <= k <= 8
+
+// out[i][q] = scale_i sum_s part[(s np + i) k + q], scale_i = src[i].y (/ div[i])
+__global__ void k_map_fin(const double* __restrict__ part, int splits, int64_t np, int dk,
+                          const float4* __restrict__ src, const double* __restrict__ div, float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  double sc = (double)src[i].y;
+  if (div) sc /= div[i];
+  for (int q = 0; q < dk; ++q) {
+    double acc = 0.0;
+    for (int s = 0; s < splits; ++s) acc += part[((int64_t)s * np + i) * dk + q];
+    out[i * dk + q] = (float)(sc * acc);
+  }
+}
+
+// inner weights of side 1: 1 / S_i = q_i / r_i, in the g2row layout
+__global__ void k_map_rowweights(const float4* __restrict__ g2row, const double* __restrict__ r, int64_t n,
+                                 float4* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 g = g2row[i];
+  out[i] = make_float4(g.x, (float)((double)g.y / r[i]), g.z, g.w);
+}
+
+// stored cost, side 0: one warp per row, sum_j 2^{v_ij} w_j V_j, times q_i / r_i
+template <int DK>
+__global__ void __launch_bounds__(kThreads)
+k_dense_map_rows(const float* __restrict__ C, int64_t ldc, int64_t n, int64_t m, const float4* __restrict__ colq,
+                 const float4* __restrict__ g2row, const double* __restrict__ r, const float* __restrict__ V,
+                 float* __restrict__ out, const DevState* __restrict__ dev, const Consts k) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+  if (i >= n) return;  // warp-uniform
+  const SweepParams sp = make_sweep_params(sweep_kappa(dev->kappa, k), k);
+  const float4 gr = g2row[i];
+  const float* crow = C + i * ldc;
+  double acc[DK];
+#pragma unroll
+  for (int q = 0; q < DK; ++q) acc[q] = 0.0;
+  for (int64_t j0 = 0; j0 < m; j0 += 32 * 64) {
+    float a[DK];
+#pragma unroll
+    for (int q = 0; q < DK; ++q) a[q] = 0.f;
+    const int64_t j1 = j0 + 32 * 64 < m ? j0 + 32 * 64 : m;
+    for (int64_t j = j0 + lane; j < j1; j += 32) {
+      const float4 cd = colq[j];
+      const float z = crow[j];
+      const float v = __fmaf_rn(sp.alA, z, __fmaf_rn(sp.ahA, z, -(gr.x + cd.x)));
+      const float e = ex2(v) * cd.y;
+#pragma unroll
+      for (int q = 0; q < DK; ++q) a[q] = __fmaf_rn(e, V[j * DK + q], a[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < DK; ++q) acc[q] += (double)a[q];
+  }
+  const double sc = (double)gr.y / r[i];
+#pragma unroll
+  for (int q = 0; q < DK; ++q) {
+    double v = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) out[i * DK + q] = (float)(sc * v);
+  }
+}
+
+// stored cost, side 1: one thread per column, sum_i 2^{v_ij} U_i / S_i, times w_j
+template <int DK>
+__global__ void __launch_bounds__(kThreads)
+k_dense_map_cols(const float* __restrict__ C, int64_t ldc, int64_t n, int64_t m, const float4* __restrict__ colq,
+                 const float4* __restrict__ g2row, const double* __restrict__ r, const float* __restrict__ U,
+                 float* __restrict__ out, const DevState* __restrict__ dev, const Consts k) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  const SweepParams sp = make_sweep_params(sweep_kappa(dev->kappa, k), k);
+  const float4 cd = colq[j];
+  double acc[DK];
+#pragma unroll
+  for (int q = 0; q < DK; ++q) acc[q] = 0.0;
+  for (int64_t i0 = 0; i0 < n; i0 += 64) {
+    float a[DK];
+#pragma unroll
+    for (int q = 0; q < DK; ++q) a[q] = 0.f;
+    const int64_t i1 = i0 + 64 < n ? i0 + 64 : n;
+    for (int64_t i = i0; i < i1; ++i) {
+      const float4 gr = g2row[i];
+      const float z = C[i * ldc + j];
+      const float v = __fmaf_rn(sp.alA, z, __fmaf_rn(sp.ahA, z, -(gr.x + cd.x)));
+      const float e = ex2(v) * (float)((double)gr.y / r[i]);
+#pragma unroll
+      for (int q = 0; q < DK; ++q) a[q] = __fmaf_rn(e, U[i * DK + q], a[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < DK; ++q) acc[q] += (double)a[q];
+  }
+#pragma unroll
+  for (int q = 0; q < DK; ++q) out[j * DK + q] = (float)((double)cd.y * acc[q]);
+}
+
+template <int DK>
+static cudaError_t launch_map_k(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int cur,
+                                const float* V, float* out, int side, cudaStream_t st) {
+  if (k.kind == COST_DENSE) {
+    if (side == 0)
+      k_dense_map_rows<DK><<<(unsigned)cdiv(k.n, kThreads / 32), kThreads, 0, st>>>(
+          in.C, in.ldc, k.n, k.m, w.colq[cur], w.g2row, in.r, V, out, w.dev, k);
+    else
+      k_dense_map_cols<DK><<<(unsigned)cdiv(k.m, kThreads), kThreads, 0, st>>>(
+          in.C, in.ldc, k.n, k.m, w.colq[cur], w.g2row, in.r, V, out, w.dev, k);
+    return cudaGetLastError();
+  }
+  if (side == 0) {
+    // outer = rows (x), inner = columns (y): weights w_j of colq, outer offsets RqA of g2row
+    SweepIO io;
+    for (int b = 0; b < 2; ++b) { io.off2[b] = nullptr; io.off4[b] = w.g2row; io.indat[b] = w.colq[b]; }
+    cudaError_t e = launch_pts<M_GRAD, DK>(in.x, in.y, k.n, k.m, k.d, io, w.rowpart, nullptr, g.rows_split, w.dev,
+                                           k, st, V);
+    if (e != cudaSuccess) return e;
+    k_map_fin<<<(unsigned)cdiv(k.n, 256), 256, 0, st>>>(w.rowpart, g.rows_split, k.n, DK, w.g2row, in.r, out);
+    return cudaGetLastError();
+  }
+  // outer = columns (y), inner = rows (x) with weights 1 / S_i (in rowpart, free here)
+  float4* rw = reinterpret_cast<float4*>(w.rowpart);
+  k_map_rowweights<<<(unsigned)cdiv(k.n, 256), 256, 0, st>>>(w.g2row, in.r, k.n, rw);
+  SweepIO io;
+  for (int b = 0; b < 2; ++b) { io.off2[b] = nullptr; io.off4[b] = w.colq[b]; io.indat[b] = rw; }
+  cudaError_t e = launch_pts<M_GRAD, DK>(in.y, in.x, k.m, k.n, k.d, io, w.colpart, nullptr, g.cols_split, w.dev, k,
+                                         st, V);
+  if (e != cudaSuccess) return e;
+  k_map_fin<<<(unsigned)cdiv(k.m, 256), 256, 0, st>>>(w.colpart, g.cols_split, k.m, DK, w.colq[cur], nullptr, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_map(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int cur, const float* V,
+                       int dk, float* out, int side, cudaStream_t st) {
+  switch (dk) {
+    case 1: return launch_map_k<1>(in, k, w, g, cur, V, out, side, st);
+    case 2: return launch_map_k<2>(in, k, w, g, cur, V, out, side, st);
+    case 3: return launch_map_k<3>(in, k, w, g, cur, V, out, side, st);
+    case 4: return launch_map_k<4>(in, k, w, g, cur, V, out, side, st);
+    case 5: return launch_map_k<5>(in, k, w, g, cur, V, out, side, st);
+    case 6: return launch_map_k<6>(in, k, w, g, cur, V, out, side, st);
+    case 7: return launch_map_k<7>(in, k, w, g, cur, V, out, side, st);
+    case 8: return launch_map_k<8>(in, k, w, g, cur, V, out, side, st);
     default: return cudaErrorNotSupported;
   }
 }

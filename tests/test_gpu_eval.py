@@ -1,5 +1,5 @@
-"""lamp_round (Alg. 3) and lamp_dual (App. B, Eqs. def:dual_spp / def:dual_spp_e) through
-the C ABI against the FP64 oracle.
+"""lamp_round (Alg. 3), lamp_dual (App. B, Eqs. def:dual_spp / def:dual_spp_e) and
+lamp_apply_map (App. E colour transfer) through the C ABI against the FP64 oracle.
 
 The GPU context is put on the oracle's own state at iteration T (lamp_set_state with
 the oracle's nu, theta, kappa), so both sides evaluate the same X^T; the oracle rounds
@@ -144,3 +144,36 @@ def test_round_leaves_the_state_alone():
     assert np.array_equal(sa["row_shifts"], sb["row_shifts"])
     a.close()
     b.close()
+
+
+MAP_CASES = [
+    # (case of CASES, k)
+    (CASES[0], 3), (CASES[1], 1), (CASES[2], 8), (CASES[3], 2), (CASES[4], 5), (CASES[5], 3),
+]
+
+
+@pytest.mark.parametrize("case,kv", MAP_CASES, ids=[f"{c[0]}-k{k}" for c, k in MAP_CASES])
+def test_apply_map_matches_oracle(case, kv):
+    """lamp_apply_map: p V and p^T U (App. E colour transfer) against the dense oracle p."""
+    import torch
+
+    w, C, s, K, st, sol = _setup(case)
+    p = O.dual_to_primal(C, K, st.kappa, st.nu)[0]
+    rng = np.random.default_rng(kv + w.n)
+    V = rng.uniform(-1.0, 1.0, size=(w.m, kv)).astype(np.float32)
+    U = rng.uniform(0.0, 1.0, size=(w.n, kv)).astype(np.float32)
+    out0 = sol.apply_map(torch.from_numpy(V).cuda(), side=0).cpu().numpy().astype(np.float64)
+    out1 = sol.apply_map(torch.from_numpy(U).cuda(), side=1).cpu().numpy().astype(np.float64)
+    ref0 = p @ V.astype(np.float64)
+    ref1 = p.T @ U.astype(np.float64)
+    # exponent error of the on-the-fly float32 cost at kappa_T (dot form), see _dot_slack
+    rel = 1e-5 + 4.0 * st.kappa * _dot_slack(w, s)
+    assert np.abs(out0 - ref0).max() <= rel * np.abs(ref0).max(), np.abs(out0 - ref0).max()
+    assert np.abs(out1 - ref1).max() <= rel * np.abs(ref1).max(), np.abs(out1 - ref1).max()
+    # p is row-stochastic, and p^T r = col(diag(r) p)
+    ones = sol.apply_map(torch.ones((w.m, 1), dtype=torch.float32, device="cuda"), side=0).cpu().numpy()
+    assert np.abs(ones - 1.0).max() <= 1e-6
+    colr = sol.apply_map(torch.from_numpy(w.r.astype(np.float32)[:, None]).cuda(), side=1).cpu().numpy()[:, 0]
+    colX = (w.r[:, None] * p).sum(axis=0)
+    assert np.abs(colr - colX).max() <= rel * colX.max()
+    sol.close()
