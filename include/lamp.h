@@ -61,7 +61,13 @@ typedef struct lamp_ctx lamp_ctx;
 /* How the cost matrix is given. */
 typedef enum {
   LAMP_COST_DENSE = 0,    /* stored n x m float32 matrix C, row-major with leading dimension ldc */
-  LAMP_COST_SQEUCLID = 1  /* C_ij = cost_scale * |x_i - y_j|^2 generated on the fly from points */
+  LAMP_COST_SQEUCLID = 1, /* C_ij = cost_scale * |x_i - y_j|^2 generated on the fly from points */
+  LAMP_COST_L1 = 2,       /* C_ij = cost_scale * sum_k |x_ik - y_jk|  (App. E.2 metric comparison) */
+  LAMP_COST_LINF = 3,     /* C_ij = cost_scale * max_k |x_ik - y_jk|  (App. E.2 metric comparison) */
+  LAMP_COST_COSINE = 4    /* C_ij = cost_scale * (1 - x_i.y_j / (|x_i| |y_j|))  (App. E.2 cell omics);
+                             points must be nonzero.  Evaluated as cost_scale * |u_i - v_j|^2 with
+                             u = x / (sqrt 2 |x|), v = y / (sqrt 2 |y|): the SQEUCLID machinery on
+                             normalised copies the context owns */
 } lamp_cost_kind;
 
 /* Arithmetic of the cost generation for LAMP_COST_SQEUCLID. */
@@ -74,15 +80,17 @@ typedef enum {
 /*
  * Problem data (Section 2.1).  All pointers are DEVICE pointers and borrowed.
  *   n, m      number of source / target supports, n >= 1, m >= 1, n*m < 2^62.
- *   d         point dimension for LAMP_COST_SQEUCLID (1 <= d <= 64); ignored for DENSE.
+ *   d         point dimension of the point-cloud kinds (1 <= d <= 64); ignored for DENSE.
  *   kind      lamp_cost_kind.
  *   C, ldc    DENSE: row-major n x m float32, entry (i,j) at C[i*ldc + j], ldc >= m,
  *             entries >= 0 and finite (C in R_+^{n x m}, Alg. 2).
- *   x, y      SQEUCLID: row-major n x d and m x d float32 point coordinates.
+ *   x, y      point-cloud kinds: row-major n x d and m x d float32 point coordinates.
  *   r, c      float64 marginals, entries > 0, each summing to 1 within 1e-9
  *             (r in Delta^n, c in Delta^m with full support, Lemma l1_prob_equiv).
- *   cost_scale  SQEUCLID multiplier s of |x - y|^2: s > 0 uses s as given; s = 0
- *             means 1; s < 0 means 1 / max_ij |x_i - y_j|^2 (cost normalised to max 1).
+ *   cost_scale  multiplier s of a point-cloud cost: s > 0 uses s as given; s = 0
+ *             means 1; s < 0 means 1 / max_ij of the unscaled cost (normalised to max 1).
+ * LAMP_PREC_BF16_TC applies to SQEUCLID and COSINE; L1 and LINF use the float32 direct
+ * form (packed f32x2 sweeps for d <= 8).  lamp_grad needs SQEUCLID.
  */
 typedef struct {
   int64_t n, m, d;

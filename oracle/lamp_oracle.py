@@ -16,7 +16,7 @@ definitions and algorithms, in the paper's order and notation:
   dual mirror map  tanh(2 tau K / c^alpha (col - c) + atanh theta0) (Eq. def:closed_form_opt)
   tclip(theta, beta) = clip to [-tanh(beta/2), tanh(beta/2)]       (Section 3.1)
 
-Readings of passages that are silent, ambiguous or garbled (listed in the design doc):
+Readings of passages that are silent, ambiguous or garbled:
   * kappa_0 = 0 stands for eta_0 = infinity, so X^0 = diag(r) (1/m).
   * beta defaults to 1.1 (App. E.2), the clip bound is tanh(0.55).
   * tau1 = tau2 = 1/(2K) and alpha = 0.01 by default, for eta = 0 and eta > 0.
@@ -38,7 +38,7 @@ import numpy as np
 
 __all__ = [
     "LampParams", "LampState", "StepInfo",
-    "sqeuclid_cost", "cost_matrix", "sup_norm",
+    "sqeuclid_cost", "l1_cost", "linf_cost", "cosine_cost", "cost_matrix", "sup_norm",
     "kappa_next", "kappa_closed_form", "log_normalizers", "dual_to_primal", "col_r", "row_sums",
     "dual_mirror_map", "tclip", "calpha_of", "resolve_params",
     "lamp_initial_state", "lamp_step", "lamp_run", "lamp_solve",
@@ -69,6 +69,35 @@ def sqeuclid_cost(x: np.ndarray, y: np.ndarray, scale: float = 1.0, chunk: int =
     if scale != 1.0:
         out *= scale
     return out
+
+
+def l1_cost(x: np.ndarray, y: np.ndarray, scale: float = 1.0) -> np.ndarray:
+    """C_ij = scale * sum_k |x_ik - y_jk| (the l1 ground cost of App. E.2), in float64."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    out = np.zeros((x.shape[0], y.shape[0]))
+    for k in range(x.shape[1]):
+        out += np.abs(x[:, None, k] - y[None, :, k])
+    return out * scale
+
+
+def linf_cost(x: np.ndarray, y: np.ndarray, scale: float = 1.0) -> np.ndarray:
+    """C_ij = scale * max_k |x_ik - y_jk| (the l-infinity ground cost of App. E.2), in float64."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    out = np.zeros((x.shape[0], y.shape[0]))
+    for k in range(x.shape[1]):
+        out = np.maximum(out, np.abs(x[:, None, k] - y[None, :, k]))
+    return out * scale
+
+
+def cosine_cost(x: np.ndarray, y: np.ndarray, scale: float = 1.0) -> np.ndarray:
+    """C_ij = scale * (1 - <x_i, y_j> / (|x_i| |y_j|)) (the cosine ground cost of App. E.2), in float64."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    nx = np.sqrt((x * x).sum(axis=1))
+    ny = np.sqrt((y * y).sum(axis=1))
+    return (1.0 - (x @ y.T) / (nx[:, None] * ny[None, :])) * scale
 
 
 def sqeuclid_cost_expanded(x: np.ndarray, y: np.ndarray, scale: float = 1.0) -> np.ndarray:

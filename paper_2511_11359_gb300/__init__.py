@@ -34,7 +34,7 @@ __all__ = [
     "LampError", "Lamp", "LampHost", "LampOT", "lamp_ot_loss", "lib", "library_path",
     "LAMP_OK", "LAMP_E_INVALID", "LAMP_E_CUDA", "LAMP_E_NOMEM", "LAMP_E_NOT_CONVERGED",
     "LAMP_E_NUMERIC", "LAMP_E_TIMEOUT", "LAMP_E_UNSUPPORTED",
-    "COST_DENSE", "COST_SQEUCLID", "PREC_FP32", "PREC_BF16_TC", "EXPORTED_SYMBOLS", "selftest_wait_timeout",
+    "COST_DENSE", "COST_SQEUCLID", "COST_L1", "COST_LINF", "COST_COSINE", "PREC_FP32", "PREC_BF16_TC", "EXPORTED_SYMBOLS", "selftest_wait_timeout",
 ]
 
 LAMP_OK = 0
@@ -47,6 +47,10 @@ LAMP_E_TIMEOUT = 6
 LAMP_E_UNSUPPORTED = 7
 COST_DENSE = 0
 COST_SQEUCLID = 1
+COST_L1 = 2
+COST_LINF = 3
+COST_COSINE = 4
+_POINT_COSTS = {"sqeuclid": COST_SQEUCLID, "l1": COST_L1, "linf": COST_LINF, "cosine": COST_COSINE}
 PREC_FP32 = 0
 PREC_BF16_TC = 1
 
@@ -183,12 +187,14 @@ class Lamp:
     """One LAMP problem on the current CUDA device (lamp_create).
 
     Either ``C`` (n x m float32, row-major, >= 0) or points ``x`` (n x d) and
-    ``y`` (m x d) float32 CUDA tensors, plus float64 CUDA marginals ``r``, ``c``.
+    ``y`` (m x d) float32 CUDA tensors with a ground ``cost`` ("sqeuclid", "l1", "linf",
+    "cosine"), plus float64 CUDA marginals ``r``, ``c``.
     The tensors are borrowed: this object keeps references to them.
     Keyword parameters are those of lamp_params (eta, tau1, tau2, alpha, beta,
     tol, max_iter, check_every, prec, K)."""
 
-    def __init__(self, r, c, *, x=None, y=None, C=None, cost_scale: float = 1.0, stream=None, **params):
+    def __init__(self, r, c, *, x=None, y=None, C=None, cost_scale: float = 1.0, cost: str = "sqeuclid",
+                 stream=None, **params):
         import torch
 
         self._keep = [r, c, x, y, C]
@@ -211,7 +217,9 @@ class Lamp:
             for t in (x, y):
                 if t is None or t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
                     raise ValueError("x and y must be contiguous float32 CUDA tensors")
-            prob.kind = COST_SQEUCLID
+            if cost not in _POINT_COSTS:
+                raise ValueError(f"cost must be one of {sorted(_POINT_COSTS)}")
+            prob.kind = _POINT_COSTS[cost]
             prob.x = _ptr(x)
             prob.y = _ptr(y)
             prob.d = x.shape[1]

@@ -43,6 +43,10 @@ struct lamp_ctx {
   // float32 copies of the rounded points, and their TMA descriptors
   void* xb = nullptr;
   void* yb = nullptr;
+  // the public cost kind; LAMP_COST_COSINE: unit-scaled copies of the points (see lamp.h)
+  int pub_kind = 0;
+  float* xn = nullptr;
+  float* yn = nullptr;
   float* xr = nullptr;
   float* yr = nullptr;
   alignas(64) unsigned char map_x[128];
@@ -110,7 +114,7 @@ static int validate(const lamp_problem* pr, const lamp_params* pa, bool device_p
   if (pr->n > (int64_t(1) << 31) || pr->m > (int64_t(1) << 31))
     return fail(nullptr, LAMP_E_INVALID, "n and m must be <= 2^31");
   if ((double)pr->n * (double)pr->m >= 4.0e18) return fail(nullptr, LAMP_E_INVALID, "n*m too large");
-  if (pr->kind != LAMP_COST_DENSE && pr->kind != LAMP_COST_SQEUCLID)
+  if (pr->kind < LAMP_COST_DENSE || pr->kind > LAMP_COST_COSINE)
     return fail(nullptr, LAMP_E_INVALID, "unknown cost kind %d", pr->kind);
   if (!pr->r || !pr->c) return fail(nullptr, LAMP_E_INVALID, "r and c must be non-null");
   if (pr->kind == LAMP_COST_DENSE) {
@@ -118,7 +122,7 @@ static int validate(const lamp_problem* pr, const lamp_params* pa, bool device_p
     if (pr->ldc < pr->m) return fail(nullptr, LAMP_E_INVALID, "ldc (%lld) < m (%lld)", (long long)pr->ldc,
                                      (long long)pr->m);
   } else {
-    if (!pr->x || !pr->y) return fail(nullptr, LAMP_E_INVALID, "SQEUCLID cost needs x and y");
+    if (!pr->x || !pr->y) return fail(nullptr, LAMP_E_INVALID, "point-cloud costs need x and y");
     if (pr->d < 1 || pr->d > 64) return fail(nullptr, LAMP_E_INVALID, "d must be in [1, 64] (d=%lld)",
                                              (long long)pr->d);
     if (!std::isfinite(pr->cost_scale)) return fail(nullptr, LAMP_E_INVALID, "cost_scale must be finite");
@@ -134,8 +138,8 @@ static int validate(const lamp_problem* pr, const lamp_params* pa, bool device_p
     return fail(nullptr, LAMP_E_INVALID, "check_every must be in [1, 100000]");
   if (pa->prec != LAMP_PREC_FP32 && pa->prec != LAMP_PREC_BF16_TC)
     return fail(nullptr, LAMP_E_INVALID, "unknown precision %d", pa->prec);
-  if (pa->prec == LAMP_PREC_BF16_TC && pr->kind != LAMP_COST_SQEUCLID)
-    return fail(nullptr, LAMP_E_INVALID, "LAMP_PREC_BF16_TC applies to LAMP_COST_SQEUCLID only");
+  if (pa->prec == LAMP_PREC_BF16_TC && pr->kind != LAMP_COST_SQEUCLID && pr->kind != LAMP_COST_COSINE)
+    return fail(nullptr, LAMP_E_INVALID, "LAMP_PREC_BF16_TC applies to LAMP_COST_SQEUCLID and LAMP_COST_COSINE only");
   if (!(pa->K >= 0.0) || !std::isfinite(pa->K)) return fail(nullptr, LAMP_E_INVALID, "K must be >= 0");
   if (pa->tau1 > 0.0 && pa->tau1 * pa->eta > 1.0) return fail(nullptr, LAMP_E_INVALID, "tau1 * eta must be <= 1");
   (void)device_ptrs;
@@ -249,12 +253,17 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
     }
   }
   Consts& k = ctx->k;
+  // point-cloud kinds run as COST_SQEUCLID internally with a ground-cost op (l1, l-inf) or
+  // on unit-scaled points (cosine)
+  const bool pts = prob->kind != LAMP_COST_DENSE;
+  ctx->pub_kind = prob->kind;
   k.n = prob->n;
   k.m = prob->m;
-  k.d = prob->kind == LAMP_COST_SQEUCLID ? (int32_t)prob->d : 0;
-  k.kind = prob->kind;
-  // direct-form cost (z = |x - y|^2) for small d; dot form x.y above
-  k.zdot = (prob->kind == LAMP_COST_SQEUCLID && (prob->d > 8 || params->prec == LAMP_PREC_BF16_TC)) ? 1 : 0;
+  k.d = pts ? (int32_t)prob->d : 0;
+  k.kind = pts ? COST_SQEUCLID : COST_DENSE;
+  k.cost_op = prob->kind == LAMP_COST_L1 ? 1 : prob->kind == LAMP_COST_LINF ? 2 : 0;
+  // direct-form cost (z = |x - y|^2) for small d; dot form x.y above (|x - y|^2 only)
+  k.zdot = (pts && k.cost_op == 0 && (prob->d > 8 || params->prec == LAMP_PREC_BF16_TC)) ? 1 : 0;
   k.shared_shift = uses_direct_sweeps(k, params->prec) ? 1 : 0;
   k.eta = params->eta;
   k.alpha = params->alpha;
@@ -272,7 +281,7 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
     ctx->owned = true;
     size_t na = prob->kind == LAMP_COST_DENSE ? (size_t)prob->n * prob->m : (size_t)prob->n * prob->d;
     if ((rc = dalloc(ctx, &ctx->own_a, na))) return bail(rc);
-    if (prob->kind == LAMP_COST_SQEUCLID && (rc = dalloc(ctx, &ctx->own_b, (size_t)prob->m * prob->d)))
+    if (pts && (rc = dalloc(ctx, &ctx->own_b, (size_t)prob->m * prob->d)))
       return bail(rc);
     if ((rc = dalloc(ctx, &ctx->own_r, (size_t)prob->n))) return bail(rc);
     if ((rc = dalloc(ctx, &ctx->own_c, (size_t)prob->m))) return bail(rc);
@@ -293,7 +302,7 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
     if (e != cudaSuccess) return bail(fail(ctx, LAMP_E_CUDA, "input copy: %s", cudaGetErrorString(e)));
     in.C = prob->kind == LAMP_COST_DENSE ? ctx->own_a : nullptr;
     in.ldc = prob->m;
-    in.x = prob->kind == LAMP_COST_SQEUCLID ? ctx->own_a : nullptr;
+    in.x = pts ? ctx->own_a : nullptr;
     in.y = ctx->own_b;
     in.r = ctx->own_r;
     in.c = ctx->own_c;
@@ -417,6 +426,24 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
     ctx->Hr = H;
   }
 
+  // cosine cost: every kernel reads unit-scaled copies u = x / (sqrt 2 |x|), v = y / (sqrt 2 |y|)
+  // (then |u - v|^2 = 1 - cos(x, y), see lamp.h)
+  if (ctx->pub_kind == LAMP_COST_COSINE) {
+    if ((rc = dalloc(ctx, &ctx->xn, n * (size_t)k.d))) return bail(rc);
+    if ((rc = dalloc(ctx, &ctx->yn, m * (size_t)k.d))) return bail(rc);
+    unsigned int* bad = reinterpret_cast<unsigned int*>(w.scratch);
+    unsigned int hbad = 0;
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned int), ctx->stream);
+    if (e == cudaSuccess) e = launch_unit_rows(in.x, k.n, k.d, ctx->xn, bad, ctx->stream);
+    if (e == cudaSuccess) e = launch_unit_rows(in.y, k.m, k.d, ctx->yn, bad, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return bail(fail(ctx, LAMP_E_CUDA, "cosine normalisation: %s", cudaGetErrorString(e)));
+    if (hbad) return bail(fail(ctx, LAMP_E_INVALID, "cosine cost needs nonzero finite points (%u are not)", hbad));
+    in.x = ctx->xn;
+    in.y = ctx->yn;
+  }
+
   // bf16 copies for the tensor-core sweeps; the float32 kernels (K pass, prime pass,
   // gradient) then read the float32 copies of the rounded points, so every kernel
   // solves the problem of the rounded points
@@ -441,8 +468,8 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
     cudaError_t e = launch_norms(in, k, w, ctx->stream);
     if (e != cudaSuccess) return bail(fail(ctx, LAMP_E_CUDA, "norms: %s", cudaGetErrorString(e)));
     bool need_K = !(params->K > 0.0);
-    bool need_scale = prob->kind == LAMP_COST_SQEUCLID && prob->cost_scale < 0.0;
-    double s = prob->kind == LAMP_COST_SQEUCLID ? (prob->cost_scale > 0.0 ? prob->cost_scale : 1.0) : 1.0;
+    bool need_scale = pts && prob->cost_scale < 0.0;
+    double s = pts ? (prob->cost_scale > 0.0 ? prob->cost_scale : 1.0) : 1.0;
     double Dmax = NAN, Dmin = NAN;
     if (need_K || need_scale || prob->kind == LAMP_COST_DENSE) {
       k.K = 1.0;
@@ -707,7 +734,7 @@ extern "C" int lamp_objective(lamp_ctx* ctx, double out[8]) {
 
 extern "C" int lamp_grad(lamp_ctx* ctx, float* dx, float* dy) {
   if (!ctx) return fail(nullptr, LAMP_E_INVALID, "lamp_grad: null context");
-  if (ctx->k.kind != COST_SQEUCLID) return fail(ctx, LAMP_E_UNSUPPORTED, "lamp_grad needs LAMP_COST_SQEUCLID");
+  if (ctx->pub_kind != LAMP_COST_SQEUCLID) return fail(ctx, LAMP_E_UNSUPPORTED, "lamp_grad needs LAMP_COST_SQEUCLID");
   if (ctx->k.d > 8) return fail(ctx, LAMP_E_UNSUPPORTED, "lamp_grad supports d <= 8 in this build");
   int rc = evaluate(ctx);
   if (rc) return rc;
@@ -785,9 +812,20 @@ extern "C" int lamp_step_host(lamp_ctx* ctx, const float* C_or_x, const float* y
     CK(cudaMemcpyAsync(ctx->own_b, y, (size_t)k.m * k.d * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->own_r, r, k.n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->own_c, c, k.m * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  const float* px = ctx->own_a;
+  const float* py = ctx->own_b;
+  if (ctx->pub_kind == LAMP_COST_COSINE) {
+    // the same normalisation as at creation (the data describe the same problem)
+    CK(launch_unit_rows(ctx->own_a, k.n, k.d, ctx->xn, reinterpret_cast<unsigned int*>(ctx->w.scratch),
+                        ctx->stream));
+    CK(launch_unit_rows(ctx->own_b, k.m, k.d, ctx->yn, reinterpret_cast<unsigned int*>(ctx->w.scratch),
+                        ctx->stream));
+    px = ctx->xn;
+    py = ctx->yn;
+  }
   if (ctx->prec == LAMP_PREC_BF16_TC) {
-    CK(tc_convert(ctx->own_a, k.n, k.d, ctx->xr, ctx->xb, ctx->stream));
-    CK(tc_convert(ctx->own_b, k.m, k.d, ctx->yr, ctx->yb, ctx->stream));
+    CK(tc_convert(px, k.n, k.d, ctx->xr, ctx->xb, ctx->stream));
+    CK(tc_convert(py, k.m, k.d, ctx->yr, ctx->yb, ctx->stream));
   }
   int rc = lamp_iterate(ctx, iters);
   if (rc) return rc;

@@ -75,7 +75,9 @@ struct Consts {
   // same_kappa = 1 gives stream B stream A's kappa (two weightings of one exponent)
   double kap_ovr = -1.0;
   int32_t same_kappa = 0;
-  int32_t pad = 0;
+  // point-cloud ground cost of the direct form: 0 |x - y|^2, 1 sum_k |x_k - y_k| (l1),
+  // 2 max_k |x_k - y_k| (l-inf)
+  int32_t cost_op = 0;
 };
 
 // Parameters of one iteration's sweeps, derived from kappa_t alone.
@@ -303,6 +305,8 @@ struct Inputs {
 
 // ---- launchers (lamp_kernels.cu) ----
 cudaError_t launch_norms(const Inputs& in, const Consts& k, const Work& w, cudaStream_t st);
+// cosine cost: out_i = P_i / (sqrt 2 |P_i|); rows with a zero or non-finite norm are counted in *bad
+cudaError_t launch_unit_rows(const float* P, int64_t np, int d, float* out, unsigned int* bad, cudaStream_t st);
 cudaError_t launch_kmax(const Inputs& in, const Consts& k, const Work& w, const Geometry& g,
                         int prec, cudaStream_t st);
 cudaError_t launch_check_marginals(const Inputs& in, const Consts& k, const Work& w, cudaStream_t st);
@@ -352,5 +356,11 @@ int tile_outer(const Consts& k, int prec);
 int tile_inner(const Consts& k, int prec);
 // whether the packed direct-form sweeps serve this problem (then Consts::shared_shift = 1)
 bool uses_direct_sweeps(const Consts& k, int prec);
+// packed direct-form sweeps (lamp_direct.cu): inner tile, outer points per CTA, occupancy, launch
+constexpr int kDirectTile = 128;
+int direct_outer(int d);
+int direct_blocks_per_sm();
+cudaError_t launch_direct_sweep(bool rows, int eval, const Inputs& in, const Consts& k, const Work& w,
+                                const Geometry& g, cudaStream_t st);
 
 }  // namespace lamp

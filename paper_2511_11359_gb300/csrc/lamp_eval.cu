@@ -155,6 +155,36 @@ k_round_dense_bilinear(const float* __restrict__ C, int64_t ldc, int64_t n, int6
   if (lane == 0) rowterm[i] = acc * dr[i];
 }
 
+// delta_r^T C delta_c for a point-cloud cost without a closed form (l1, l-inf): one warp
+// per row, the cost recomputed in float32, float64 accumulation per lane
+__global__ void __launch_bounds__(kT)
+k_round_pts_bilinear(const float* __restrict__ x, const float* __restrict__ y, int d, int64_t n, int64_t m,
+                     const double* __restrict__ dr, const double* __restrict__ dc, double* __restrict__ rowterm,
+                     const Consts k) {
+  __shared__ float sx[kT / 32][64];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * (kT / 32) + wid;
+  if (i >= n) return;  // warp-uniform; no block-wide barrier below
+  for (int q = lane; q < d; q += 32) sx[wid][q] = x[i * d + q];
+  __syncwarp();
+  double acc = 0.0;
+  for (int64_t j0 = 0; j0 < m; j0 += 32 * 32) {
+    float a = 0.f;
+    const int64_t j1 = j0 + 32 * 32 < m ? j0 + 32 * 32 : m;
+    for (int64_t j = j0 + lane; j < j1; j += 32) {
+      float z = 0.f;
+      for (int q = 0; q < d; ++q) {
+        const float ad = fabsf(sx[wid][q] - y[j * d + q]);
+        z = k.cost_op == 1 ? z + ad : fmaxf(z, ad);
+      }
+      a = __fmaf_rn(z, (float)dc[j], a);
+    }
+    acc += (double)a;
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) rowterm[i] = k.s * acc * dr[i];
+}
+
 // out[q] = sum over blocks b of part[b * nf + q], in a fixed order (one block per field)
 __global__ void __launch_bounds__(kT) k_fields(const double* __restrict__ part, int64_t nblocks, int nf,
                                                double* __restrict__ out) {
@@ -171,13 +201,13 @@ __global__ void k_round_final(const double* __restrict__ rowf, const double* __r
   const double ndr = rowf[0], ndc = colf[1];
   const double cpp = colf[0] + rowf[1];  // <C, X^t diag(y)>
   double bil;
-  if (k.kind == COST_SQEUCLID) {
+  if (k.kind == COST_SQEUCLID && k.cost_op == 0) {
     // sum_ij s |x_i - y_j|^2 dr_i dc_j = (sum dr s|x|^2)(sum dc) + (sum dr)(sum dc s|y|^2) - 2 s (sum dr x).(sum dc y)
     double cross = 0.0;
     for (int q = 0; q < dm; ++q) cross += rowf[3 + q] * colf[3 + q];
     bil = rowf[2] * ndc + ndr * colf[2] - 2.0 * k.s * cross;
   } else {
-    bil = densef[0];
+    bil = densef[0];  // stored cost, or l1 / l-inf point costs: one pass
   }
   out[0] = cpp + (ndr > 0.0 ? bil / ndr : 0.0);
   out[1] = ndr;
@@ -241,7 +271,9 @@ k_dual_rows(const Work w, const float2* __restrict__ rs_s, int splits, const dou
 cudaError_t launch_round(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec, int cur,
                          double* out4, double* y, double* dr, double* dc, cudaStream_t st) {
   const int nx = cur ^ 1;  // scratch parity
-  const int dm = k.kind == COST_SQEUCLID ? k.d : 0;
+  // the closed-form bilinear term needs the coordinate moments (|x - y|^2 only)
+  const bool moments = k.kind == COST_SQEUCLID && k.cost_op == 0;
+  const int dm = moments ? k.d : 0;
   const int nf = 3 + dm;
   const int64_t rb = fin_blocks(k.n), cb = fin_blocks(k.m);
   double* rowp = w.rscr;
@@ -267,10 +299,14 @@ cudaError_t launch_round(const Inputs& in, const Consts& k, const Work& w, const
   e = launch_iteration_part(in, k2, w2, g, prec, 0, 0, st);
   if (e != cudaSuccess) return e;
   k_round_rows<<<(unsigned)rb, kT, 0, st>>>(w, g.rows_split, in.r, in.x, dm, dr, rowp, k);
-  if (k.kind == COST_DENSE) {
+  if (!moments) {
     // delta_r is in rowpart[0, n) (k_round_rows); per-row terms go to rowpart[n, 2n)
-    k_round_dense_bilinear<<<(unsigned)cdiv(k.n, kT / 32), kT, 0, st>>>(in.C, in.ldc, k.n, k.m, w.rowpart,
-                                                                       dc_tmp, w.rowpart + k.n);
+    if (k.kind == COST_DENSE)
+      k_round_dense_bilinear<<<(unsigned)cdiv(k.n, kT / 32), kT, 0, st>>>(in.C, in.ldc, k.n, k.m, w.rowpart,
+                                                                         dc_tmp, w.rowpart + k.n);
+    else
+      k_round_pts_bilinear<<<(unsigned)cdiv(k.n, kT / 32), kT, 0, st>>>(in.x, in.y, k.d, k.n, k.m, w.rowpart,
+                                                                        dc_tmp, w.rowpart + k.n, k);
     k_fields<<<1, kT, 0, st>>>(w.rowpart + k.n, k.n, 1, densef);
   }
   k_fields<<<(unsigned)nf, kT, 0, st>>>(rowp, rb, nf, rowf);

@@ -177,13 +177,26 @@ k_pts_sweep(const float* __restrict__ P_out, const float* __restrict__ P_in, int
       float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
       float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
       if (DIFF) {
+        // the ground cost of the direct form (Consts::cost_op; uniform branch)
+        if (k.cost_op == 0) {
 #pragma unroll
-        for (int a = 0; a < 8; ++a)
+          for (int a = 0; a < 8; ++a)
 #pragma unroll
-          for (int b = 0; b < 8; ++b) {
-            const float df = av[a] - bv[b];
-            z[a][b] = __fmaf_rn(df, df, z[a][b]);
-          }
+            for (int b = 0; b < 8; ++b) {
+              const float df = av[a] - bv[b];
+              z[a][b] = __fmaf_rn(df, df, z[a][b]);
+            }
+        } else if (k.cost_op == 1) {
+#pragma unroll
+          for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b < 8; ++b) z[a][b] += fabsf(av[a] - bv[b]);
+        } else {
+#pragma unroll
+          for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b < 8; ++b) z[a][b] = fmaxf(z[a][b], fabsf(av[a] - bv[b]));
+        }
       } else {
 #pragma unroll
         for (int a = 0; a < 8; ++a)
@@ -299,212 +312,6 @@ k_pts_sweep(const float* __restrict__ P_out, const float* __restrict__ P_in, int
         if (tx == 0 && go < n_out) part[((int64_t)split * n_out + go) * DG + q] = v;
       }
     }
-  }
-}
-
-// ------------------------------------------------------------------------------------------
-// direct-form sweeps over point clouds with d <= 8 (LAMP_COST_SQEUCLID, float32, packed f32x2)
-//
-// Each thread owns kR(D) outer points o0 + tid + 256 r for the CTA's lifetime and
-// keeps their coordinates and exponent offsets in registers as duplicated pairs
-// (x, x).  The CTA streams the inner points through shared memory in tiles of 128
-// (64 pairs, double-buffered with cp.async) and all threads read the same inner
-// pair at the same time (broadcast loads), so one f32x2 instruction serves the two
-// entries (outer, 2p) and (outer, 2p + 1).  Per pair of entries: d subtractions
-// and d multiply-adds for z = |x - y|^2; stream A one add, two fma (compensated
-// exponent), two ex2 and one fma (weighted sum); stream B, through the shared row
-// shift (see lamp_common.cuh), one add, one fma, two ex2 and one fma.  Evaluation
-// passes also accumulate sum_i z_ij X_ij in the column sweep (two more).
-// z = sum_k (x_k - y_k)^2 is accumulated in the same k order in both sweeps, and
-// (y - x)^2 == (x - y)^2 in IEEE arithmetic, so the row and the column sweep see
-// bit-identical exponents.  The inner data are the packed-pair arrays (see Work).
-
-constexpr int kDTile = 128;          // inner points per shared-memory tile
-constexpr int kDPairs = kDTile / 2;  // pairs per tile
-constexpr int kDFold = 32;           // pairs between float-float folds of the packed sums
-
-template <int D>
-struct DirectCfg {
-  static constexpr int R = D <= 4 ? 4 : 2;  // outer points per thread
-  static constexpr int DP = (D + 1) & ~1;   // coordinates per pair record, even
-  static constexpr int REC = DP * 2 + 8;    // floats per pair record: coords [DP][2], offsets/weights A, B
-  static constexpr int OUTER = kThreads * R;
-};
-
-__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
-}
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// stage inner tile `it` (points it*128 ..) into the record buffer `rec`
-template <int D>
-__device__ __forceinline__ void direct_stage(float* rec, const float* __restrict__ P_in, int64_t n_in,
-                                             const float4* __restrict__ pairs, int64_t it, int tid) {
-  using C = DirectCfg<D>;
-  const int64_t i0 = it * kDTile;
-  for (int idx = tid; idx < kDTile * D; idx += kThreads) {
-    const int b = idx / D, k = idx - (idx / D) * D;
-    const bool ok = i0 + b < n_in;
-    const float* src = ok ? P_in + (i0 + b) * D + k : P_in;
-    cp_async4(rec + (b >> 1) * C::REC + k * 2 + (b & 1), src, ok);
-  }
-  // offsets / weights: pairs [2(i0/2 + p)] (stream A) and [2(i0/2 + p) + 1] (stream B);
-  // the pair arrays are padded to 128 entries, so a whole tile is always in bounds
-  for (int idx = tid; idx < kDPairs * 2; idx += kThreads) {
-    const int p = idx >> 1, s = idx & 1;
-    cp_async16(rec + p * C::REC + C::DP * 2 + 4 * s, pairs + (i0 >> 1) * 2 + idx);
-  }
-}
-
-// MODE = M_ROWSUM, or M_COLSUM with WC = 1 (evaluation pass: cost-weighted column sums too) or 0
-template <int MODE, int D, int WC>
-__global__ void __launch_bounds__(kThreads, 2)
-k_pts_direct(const float* __restrict__ P_out, const float* __restrict__ P_in, int64_t n_out, int64_t n_in,
-             const Work w, double* __restrict__ part, int tiles_per_split, const Consts k) {
-  using C = DirectCfg<D>;
-  constexpr int R = C::R, DP = C::DP, REC = C::REC;
-  constexpr int NACC = WC ? 3 : 2;
-  const DevState* __restrict__ dev = w.dev;
-  if (dev->done) return;
-  const int cur = dev->cur;
-  // row sweep: inner = columns (colq2 of the current state); column sweep: inner = rows (g2row2)
-  const float4* __restrict__ pairs = MODE == M_ROWSUM ? w.colq2[cur] : w.g2row2;
-  __shared__ __align__(16) float srec[2][kDPairs * REC];
-
-  const int tid = threadIdx.x;
-  const int64_t o0 = (int64_t)blockIdx.x * C::OUTER;
-  const int split = blockIdx.y;
-  const int64_t ntiles = (n_in + kDTile - 1) / kDTile;
-  const int64_t it0 = (int64_t)split * tiles_per_split;
-  const int64_t it1 = it0 + tiles_per_split < ntiles ? it0 + tiles_per_split : ntiles;
-
-  if (it0 < it1) direct_stage<D>(srec[0], P_in, n_in, pairs, it0, tid);
-  cp_async_commit();
-  if (DP > D) {  // the padding coordinate of odd d is read by the 16-byte loads, never used
-    for (int p = tid; p < 2 * kDPairs; p += kThreads) {
-      srec[p / kDPairs][(p % kDPairs) * REC + 2 * D] = 0.f;
-      srec[p / kDPairs][(p % kDPairs) * REC + 2 * D + 1] = 0.f;
-    }
-  }
-
-  const SweepParams sp = make_sweep_params(sweep_kappa(dev->kappa, k), k);
-  const uint64_t ahA2 = pk(sp.ahA, sp.ahA), alA2 = pk(sp.alA, sp.alA);
-  const float dal = (float)(sp.aB - sp.aA);  // a^B - a^A
-  const uint64_t da2 = pk(dal, dal);
-
-  // own offsets: -RqA_i (row sweep), or -BqA_j and dB_j = BqA_j - BqB_j (column sweep)
-  uint64_t x2[R][D], ownA[R], ownD[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    int64_t go = o0 + tid + (int64_t)kThreads * r;
-    if (go >= n_out) go = n_out - 1;
-#pragma unroll
-    for (int kk = 0; kk < D; ++kk) {
-      const float v = P_out[go * D + kk];
-      x2[r][kk] = pk(v, v);
-    }
-    float qa, qb;
-    if (MODE == M_ROWSUM) {
-      const float2 q = w.rowshift[cur][go];
-      qa = q.x;
-      qb = q.y;
-    } else {
-      const float4 q = w.colq[cur][go];
-      qa = q.x;
-      qb = q.z;
-    }
-    ownA[r] = pk(-qa, -qa);
-    const float db = (-qb) - (-qa);  // exact: two multiples of the grid (see lamp_common.cuh)
-    ownD[r] = pk(db, db);
-  }
-
-  float hi[R][NACC], lo[R][NACC];
-  uint64_t acc[R][NACC];
-#pragma unroll
-  for (int r = 0; r < R; ++r)
-#pragma unroll
-    for (int q = 0; q < NACC; ++q) {
-      hi[r][q] = 0.f;
-      lo[r][q] = 0.f;
-      acc[r][q] = 0ull;  // (+0, +0)
-    }
-
-  for (int64_t it = it0; it < it1; ++it) {
-    const int buf = (int)((it - it0) & 1);
-    if (it + 1 < it1) direct_stage<D>(srec[buf ^ 1], P_in, n_in, pairs, it + 1, tid);
-    cp_async_commit();
-    cp_async_wait<1>();
-    __syncthreads();
-    const float* rec = srec[buf];
-#pragma unroll 1
-    for (int p0 = 0; p0 < kDPairs; p0 += kDFold) {
-#pragma unroll 2
-      for (int p = p0; p < p0 + kDFold; ++p) {
-        const float* rp = rec + p * REC;
-        uint64_t y2[DP];
-#pragma unroll
-        for (int kk = 0; kk < DP; kk += 2) {
-          const float4 t = *reinterpret_cast<const float4*>(rp + 2 * kk);
-          y2[kk] = pk(t.x, t.y);
-          y2[kk + 1] = pk(t.z, t.w);
-        }
-        const float4 dA = *reinterpret_cast<const float4*>(rp + 2 * DP);
-        const float4 dB = *reinterpret_cast<const float4*>(rp + 2 * DP + 4);
-        const uint64_t oA2 = pk(dA.x, dA.y), wA2 = pk(dA.z, dA.w);
-        const uint64_t wB2 = pk(dB.z, dB.w);
-        // row sweep: the inner columns' BqA_j - BqB_j (exact, as for ownD)
-        uint64_t dC2 = 0ull;
-        if constexpr (MODE == M_ROWSUM) dC2 = f2sub(pk(dB.x, dB.y), oA2);
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          uint64_t df = f2sub(x2[r][0], y2[0]);
-          uint64_t z2 = f2mul(df, df);
-#pragma unroll
-          for (int kk = 1; kk < D; ++kk) {
-            df = f2sub(x2[r][kk], y2[kk]);
-            z2 = f2fma(df, df, z2);
-          }
-          const uint64_t vA = f2fma(alA2, z2, f2fma(ahA2, z2, f2add(ownA[r], oA2)));
-          const uint64_t vB = f2fma(da2, z2, f2add(vA, MODE == M_ROWSUM ? dC2 : ownD[r]));
-          const float2 vAf = upk(vA), vBf = upk(vB);
-          const uint64_t eA = pk(ex2(vAf.x), ex2(vAf.y));
-          const uint64_t eB = pk(ex2(vBf.x), ex2(vBf.y));
-          if constexpr (WC) {
-            const uint64_t pA = f2mul(eA, wA2);
-            acc[r][0] = f2add(acc[r][0], pA);
-            acc[r][2] = f2fma(z2, pA, acc[r][2]);
-          } else {
-            acc[r][0] = f2fma(eA, wA2, acc[r][0]);
-          }
-          acc[r][1] = f2fma(eB, wB2, acc[r][1]);
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-#pragma unroll
-        for (int q = 0; q < NACC; ++q) {
-          const float2 s = upk(acc[r][q]);
-          ff_add(hi[r][q], lo[r][q], s.x + s.y);
-          acc[r][q] = 0ull;
-        }
-    }
-    __syncthreads();  // every thread is done with srec[buf] before it is refilled
-  }
-  cp_async_wait<0>();
-
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int64_t go = o0 + tid + (int64_t)kThreads * r;
-    if (go >= n_out) continue;
-#pragma unroll
-    for (int q = 0; q < NACC; ++q) part[((int64_t)split * NACC + q) * n_out + go] = (double)hi[r][q] + (double)lo[r][q];
   }
 }
 
@@ -756,6 +563,20 @@ __global__ void k_norms(const float* __restrict__ P, int64_t np, int d, double* 
   nrm[i] = s;
   if (f2) f2[i] = make_float2(sf, 0.f);
   if (f4) f4[i] = make_float4(sf, 0.f, 0.f, 0.f);
+}
+
+// cosine cost: out_i = P_i / (sqrt 2 |P_i|) (float64 norm); rows with a zero or non-finite
+// norm are counted in *bad and written as zeros
+__global__ void k_unit_rows(const float* __restrict__ P, int64_t np, int d, float* __restrict__ out,
+                            unsigned int* __restrict__ bad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  double s = 0.0;
+  for (int q = 0; q < d; ++q) s += (double)P[i * d + q] * (double)P[i * d + q];
+  double sc = 0.0;
+  if (s > 0.0 && isfinite(s)) sc = 1.0 / sqrt(2.0 * s);
+  else atomicAdd(bad, 1u);
+  for (int q = 0; q < d; ++q) out[i * d + q] = (float)((double)P[i * d + q] * sc);
 }
 
 // marginal checks: sum, min, finiteness (block partials, 3 doubles per block)
@@ -1075,35 +896,14 @@ static cudaError_t launch_pts(const float* Pout, const float* Pin, int64_t nout,
   return cudaGetLastError();
 }
 
-template <int MODE, int D, int WC>
-static cudaError_t launch_direct_d(const float* Pout, const float* Pin, int64_t nout, int64_t nin, const Work& w,
-                                   double* part, int splits, const Consts& k, cudaStream_t st) {
-  int64_t tin = cdiv(nin, kDTile);
-  int tps = (int)cdiv(tin, splits);
-  dim3 grid((unsigned)cdiv(nout, DirectCfg<D>::OUTER), (unsigned)splits);
-  k_pts_direct<MODE, D, WC><<<grid, kThreads, 0, st>>>(Pout, Pin, nout, nin, w, part, tps, k);
-  return cudaGetLastError();
-}
-
-template <int MODE, int WC>
-static cudaError_t launch_direct(const float* Pout, const float* Pin, int64_t nout, int64_t nin, const Work& w,
-                                 double* part, int splits, const Consts& k, cudaStream_t st) {
-  switch (k.d) {
-    case 1: return launch_direct_d<MODE, 1, WC>(Pout, Pin, nout, nin, w, part, splits, k, st);
-    case 2: return launch_direct_d<MODE, 2, WC>(Pout, Pin, nout, nin, w, part, splits, k, st);
-    case 3: return launch_direct_d<MODE, 3, WC>(Pout, Pin, nout, nin, w, part, splits, k, st);
-    case 4: return launch_direct_d<MODE, 4, WC>(Pout, Pin, nout, nin, w, part, splits, k, st);
-    case 5: return launch_direct_d<MODE, 5, WC>(Pout, Pin, nout, nin, w, part, splits, k, st);
-    case 6: return launch_direct_d<MODE, 6, WC>(Pout, Pin, nout, nin, w, part, splits, k, st);
-    case 7: return launch_direct_d<MODE, 7, WC>(Pout, Pin, nout, nin, w, part, splits, k, st);
-    case 8: return launch_direct_d<MODE, 8, WC>(Pout, Pin, nout, nin, w, part, splits, k, st);
-    default: return cudaErrorNotSupported;
-  }
-}
-
 // the packed direct-form sweeps serve |x - y|^2 with d <= 8 in float32
 bool uses_direct_sweeps(const Consts& k, int prec) {
   return k.kind == COST_SQEUCLID && !k.zdot && prec != 1 /* LAMP_PREC_BF16_TC */ && k.d >= 1 && k.d <= 8;
+}
+
+cudaError_t launch_unit_rows(const float* P, int64_t np, int d, float* out, unsigned int* bad, cudaStream_t st) {
+  k_unit_rows<<<(unsigned)cdiv(np, 256), 256, 0, st>>>(P, np, d, out, bad);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_norms(const Inputs& in, const Consts& k, const Work& w, cudaStream_t st) {
@@ -1148,8 +948,7 @@ static cudaError_t launch_row_sweep(const Inputs& in, const Consts& k, const Wor
       k_dense_rows<M_MAX><<<grid, kThreads, 0, st>>>(in.C, in.ldc, k.n, k.m, w, cps, k);
     return cudaGetLastError();
   }
-  if (mode == M_ROWSUM && k.shared_shift)
-    return launch_direct<M_ROWSUM, 0>(in.x, in.y, k.n, k.m, w, w.rowpart, g.rows_split, k, st);
+  if (mode == M_ROWSUM && k.shared_shift) return launch_direct_sweep(true, 0, in, k, w, g, st);
   SweepIO io;
   for (int b = 0; b < 2; ++b) {
     io.off2[b] = w.rowshift[b];
@@ -1170,10 +969,7 @@ static cudaError_t launch_col_sweep(const Inputs& in, const Consts& k, const Wor
     k_dense_cols<<<grid, kThreads, 0, st>>>(in.C, in.ldc, k.n, k.m, w, rps, k);
     return cudaGetLastError();
   }
-  if (k.shared_shift) {
-    if (eval) return launch_direct<M_COLSUM, 1>(in.y, in.x, k.m, k.n, w, w.colpart, g.cols_split, k, st);
-    return launch_direct<M_COLSUM, 0>(in.y, in.x, k.m, k.n, w, w.colpart, g.cols_split, k, st);
-  }
+  if (k.shared_shift) return launch_direct_sweep(false, eval, in, k, w, g, st);
   SweepIO io;
   for (int b = 0; b < 2; ++b) {
     io.off2[b] = nullptr;
@@ -1258,9 +1054,7 @@ int sweep_blocks_per_sm(const Consts& k, int prec, int which) {
     else
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dense_cols, kThreads, 0);
   } else if (uses_direct_sweeps(k, prec)) {
-    // every instantiation is declared with __launch_bounds__(kThreads, 2) and static shared memory
-    auto kern = which == 0 ? k_pts_direct<M_ROWSUM, 8, 0> : k_pts_direct<M_COLSUM, 8, 1>;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kThreads, 0);
+    nb = direct_blocks_per_sm();
   } else {
     auto kern = which == 0 ? (k.zdot ? k_pts_sweep<M_ROWSUM, 0, false> : k_pts_sweep<M_ROWSUM, 0, true>)
                            : (k.zdot ? k_pts_sweep<M_COLSUM, 0, false> : k_pts_sweep<M_COLSUM, 0, true>);
@@ -1269,18 +1063,17 @@ int sweep_blocks_per_sm(const Consts& k, int prec, int which) {
   return nb > 0 ? nb : 1;
 }
 
-static int direct_outer(int d) { return kThreads * (d <= 4 ? DirectCfg<4>::R : DirectCfg<8>::R); }
 int tile_outer(const Consts& k, int prec) {
   return k.kind == COST_DENSE ? kDR : uses_direct_sweeps(k, prec) ? direct_outer(k.d) : kPT;
 }
 int tile_inner(const Consts& k, int prec) {
-  return k.kind == COST_DENSE ? kDChunk : uses_direct_sweeps(k, prec) ? kDTile : kPT;
+  return k.kind == COST_DENSE ? kDChunk : uses_direct_sweeps(k, prec) ? kDirectTile : kPT;
 }
 int tile_outer_cols(const Consts& k, int prec) {
   return k.kind == COST_DENSE ? kDChunk : uses_direct_sweeps(k, prec) ? direct_outer(k.d) : kPT;
 }
 int tile_inner_cols(const Consts& k, int prec) {
-  return k.kind == COST_DENSE ? kDColRows : uses_direct_sweeps(k, prec) ? kDTile : kPT;
+  return k.kind == COST_DENSE ? kDColRows : uses_direct_sweeps(k, prec) ? kDirectTile : kPT;
 }
 
 template <int DG>

@@ -91,6 +91,8 @@ extern "C" int lamp_marginals_noalloc(const lamp_problem* prob, double K, double
   using namespace lamp;
   if (!prob || !nu || !logZ_out || !col_out) return noalloc_fail(LAMP_E_INVALID, "null argument");
   if (prob->n < 1 || prob->m < 1) return noalloc_fail(LAMP_E_INVALID, "n and m must be >= 1");
+  if (prob->kind >= LAMP_COST_L1 && prob->kind <= LAMP_COST_COSINE)
+    return noalloc_fail(LAMP_E_UNSUPPORTED, "lamp_marginals_noalloc supports LAMP_COST_DENSE and LAMP_COST_SQEUCLID");
   if (prob->kind != LAMP_COST_DENSE && prob->kind != LAMP_COST_SQEUCLID)
     return noalloc_fail(LAMP_E_INVALID, "unknown cost kind");
   if (!prob->r || !prob->c) return noalloc_fail(LAMP_E_INVALID, "r and c must be non-null");

@@ -37,7 +37,8 @@ def oracle_cost(w):
     if w.kind == "dense":
         C = np.asarray(w.C, dtype=np.float64)
         return C, 1.0, float(C.max())
-    D = O.sqeuclid_cost(w.x, w.y)
+    cost = {"sqeuclid": O.sqeuclid_cost, "l1": O.l1_cost, "linf": O.linf_cost, "cosine": O.cosine_cost}[w.kind]
+    D = cost(w.x, w.y)
     s = w.cost_scale
     if s < 0:
         s = 1.0 / D.max()
@@ -55,7 +56,8 @@ def gpu_solver(w, K=None, scale=None, **params):
     r, c = dev(w.r), dev(w.c)
     if w.kind == "dense":
         return L.Lamp(r, c, C=dev(w.C), K=K, **params), C, K
-    return L.Lamp(r, c, x=dev(w.x), y=dev(w.y), cost_scale=s if scale is None else scale, K=K, **params), C, K
+    return L.Lamp(r, c, x=dev(w.x), y=dev(w.y), cost_scale=s if scale is None else scale, K=K, cost=w.kind,
+                  **params), C, K
 
 
 def gpu_solver_raw(w, K, scale=1.0, **params):
@@ -66,7 +68,7 @@ def gpu_solver_raw(w, K, scale=1.0, **params):
     r, c = dev(w.r), dev(w.c)
     if w.kind == "dense":
         return L.Lamp(r, c, C=dev(w.C), K=K, **params)
-    return L.Lamp(r, c, x=dev(w.x), y=dev(w.y), cost_scale=scale, K=K, **params)
+    return L.Lamp(r, c, x=dev(w.x), y=dev(w.y), cost_scale=scale, K=K, cost=w.kind, **params)
 
 
 def assert_pot_close(st, ref, tol=POT_TOL, what=""):
@@ -82,9 +84,14 @@ def assert_logZ_close(lz, ref, tol=LOGZ_TOL, what=""):
 
 
 def cost_error(w):
-    """max_ij |C32_ij - C_ij|: float32 evaluation of sum_k (x_ik - y_jk)^2 against float64."""
+    """max_ij |C32_ij - C_ij|: float32 evaluation of the point cost against float64
+    (|x - y|^2 by its differences; l1 / l-inf / cosine by a bound of d float32 roundings
+    of terms of the cost's size)."""
     if w.kind == "dense":
         return 0.0
+    if w.kind != "sqeuclid":
+        C, s, K = oracle_cost(w)
+        return float(2.0 * max(w.d, 2) * 2.0 ** -24 * K)
     x32 = np.asarray(w.x, np.float32)
     y32 = np.asarray(w.y, np.float32)
     d32 = np.zeros((x32.shape[0], y32.shape[0]), np.float32)

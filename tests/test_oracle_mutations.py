@@ -45,6 +45,9 @@ MUTANTS = [
      PINS.test_lamp_equals_explicit_pdmp, (16, 16, 2, 0.0)),
     ("tclip", "np.tanh(beta / 2.0)", "np.tanh(beta)", PINS.test_tclip_bounds, ()),
     ("round_factors", "X2 = X1 * y[None, :]", "X2 = X1", PINS.test_round_is_feasible_and_within_bound, (0,)),
+    ("l1_cost", "out += np.abs(", "out += (", PINS.test_point_costs_match_scipy_distances, ()),
+    ("linf_cost", "np.maximum(out, np.abs(", "np.maximum(out, (", PINS.test_point_costs_match_scipy_distances, ()),
+    ("cosine_cost", "(nx[:, None] * ny[None, :])", "(nx[:, None] * nx[:, None])", PINS.test_point_costs_match_scipy_distances, ()),
     ("round_plan", "np.outer(dr, dc) / l1", "np.outer(dc, dr).T / l1 * 0.5", PINS.test_round_is_feasible_and_within_bound, (0,)),
     ("entropy_from_normalizers", "2.0 * K * kappa", "K * kappa", PINS.test_entropy_identity, (0.0,)),
     ("saddle_dual", "- 2.0 * K * (c @ theta)", "+ 2.0 * K * (c @ theta)",

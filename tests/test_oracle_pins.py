@@ -470,3 +470,22 @@ def test_streamed_step_equals_dense_step():
     assert np.max(np.abs(got.nu - ref.nu)) < 1e-13 and np.max(np.abs(got.theta - ref.theta)) < 1e-12
     assert np.max(np.abs(A - info.A)) < 1e-15 and np.max(np.abs(lzB - info.logZ_B)) < 1e-12
     assert O.streamed_sup_norm(lambda rows: C[rows], 70, chunk=9) == K
+
+
+def test_point_costs_match_scipy_distances():
+    """l1, l-inf and cosine ground costs (App. E.2) against scipy's cdist metrics
+    'cityblock', 'chebyshev' and 'cosine' (1 - cos), an independent implementation."""
+    from scipy.spatial.distance import cdist
+
+    rng = np.random.default_rng(71)
+    for d in (1, 3, 17):
+        x = rng.normal(size=(23, d))
+        y = rng.normal(size=(19, d)) + 0.3
+        np.testing.assert_allclose(O.l1_cost(x, y), cdist(x, y, "cityblock"), rtol=1e-13, atol=1e-13)
+        np.testing.assert_allclose(O.linf_cost(x, y), cdist(x, y, "chebyshev"), rtol=1e-13, atol=1e-13)
+        np.testing.assert_allclose(O.cosine_cost(x, y), cdist(x, y, "cosine"), rtol=1e-12, atol=1e-13)
+        np.testing.assert_allclose(O.l1_cost(x, y, 0.25), 0.25 * cdist(x, y, "cityblock"), rtol=1e-13)
+    # cosine = half the squared distance of the unit-normalised points
+    u = x / np.linalg.norm(x, axis=1, keepdims=True)
+    v = y / np.linalg.norm(y, axis=1, keepdims=True)
+    np.testing.assert_allclose(O.cosine_cost(x, y), 0.5 * O.sqeuclid_cost(u, v), rtol=1e-12, atol=1e-13)

@@ -57,7 +57,8 @@ __all__ = [
 class Workload:
     """One synthetic problem instance.
 
-    kind: "sqeuclid" (points x, y given) or "dense" (stored cost C given).
+    kind: "dense" (stored cost C given), or a point-cloud ground cost with points x, y
+        given: "sqeuclid" (|x-y|^2), "l1", "linf" or "cosine".
     cost_scale: multiplier applied to |x-y|^2 by the solver; a negative value
         asks the solver to divide by the maximum cost (as in ``plain_2d``).
     eta, tol: entropic coefficient and L1 infeasibility target of the workload.
@@ -187,6 +188,18 @@ def points_problem(name: str, n: int, m: int, d: int, seed: int, dist: str = "un
                     x=np.ascontiguousarray(x, dtype=np.float32),
                     y=np.ascontiguousarray(y, dtype=np.float32),
                     cost_scale=cost_scale, eta=eta, tol=tol, seed=seed)
+
+
+def half_norm_points(n: int, d: int, seed: int, nnz: int = 32) -> np.ndarray:
+    """n points in R^d (d >= nnz) with nnz coordinates of +-1/8 at random positions and
+    random signs, the rest 0: every coordinate is exact in bf16 and |x|^2 = nnz/64 exactly
+    (1/2 for nnz = 32), so scaling to norm 1/sqrt(2) is exact (cosine-cost test points)."""
+    rng = _rng(seed)
+    x = np.zeros((n, d), np.float32)
+    for i in range(n):
+        idx = rng.choice(d, size=nnz, replace=False)
+        x[i, idx] = np.where(rng.random(nnz) < 0.5, -0.125, 0.125).astype(np.float32)
+    return x
 
 
 def dense_problem(name: str, n: int, m: int, seed: int, eta: float = 0.0, tol: float = 1e-6,
