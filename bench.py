@@ -401,6 +401,46 @@ def run_gpu(args, rank, world):
         dist.destroy_process_group()
 
 
+# the paper's Table 1: row-LSE reduction latency (ms) of its fused + warp-tiled kernel on an
+# RTX 4090 (one stream, precision not stated), for context only
+PAPER_TABLE1_FUSED_WT_MS = {1024: 0.12, 4096: 1.30, 16384: 17.13, 65536: 252.5}
+
+
+def run_lse_table(args):
+    """Row sweep (G1: row sums of both streams, i.e. two row LSEs) at the n of the paper's
+    Table 1, for a stored n x n float32 C ~ U[0,1) and for on-the-fly |x - y|^2 with
+    x, y ~ U[0,1]^3; mean CUDA-event time of the row-sweep launch over `steps` iterations."""
+    import torch
+    import paper_2511_11359_gb300 as L
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    rows = []
+    for n in sorted(PAPER_TABLE1_FUSED_WT_MS):
+        g = torch.Generator(device=dev).manual_seed(1000 + n)
+        r = torch.full((n,), 1.0 / n, dtype=torch.float64, device=dev)
+        entry = {"n": n, "paper_fused_wt_ms_rtx4090_one_stream": PAPER_TABLE1_FUSED_WT_MS[n]}
+        C = torch.rand((n, n), generator=g, device=dev, dtype=torch.float32)
+        s = L.Lamp(r, r, C=C, K=1.0)
+        s.iterate(args.warmup)
+        entry["stored_C_row_sweep_ms"] = s.time_kernels(args.steps)[0]
+        s.close()
+        del C
+        torch.cuda.empty_cache()
+        x = torch.rand((n, 3), generator=g, device=dev, dtype=torch.float32)
+        y = torch.rand((n, 3), generator=g, device=dev, dtype=torch.float32)
+        s = L.Lamp(r, r, x=x, y=y, K=3.0)
+        s.iterate(args.warmup)
+        entry["points_d3_row_sweep_ms"] = s.time_kernels(args.steps)[0]
+        s.close()
+        entry["stored_C_entries_per_s"] = n * n / (entry["stored_C_row_sweep_ms"] / 1e3)
+        entry["points_d3_entries_per_s"] = n * n / (entry["points_d3_row_sweep_ms"] / 1e3)
+        rows.append(entry)
+    print(json.dumps({"metric": "row-LSE sweep time at the shapes of the paper's Table 1 (two streams per sweep)",
+                      "unit": "ms", "higher_is_better": False, "data": "synthetic", "steps": args.steps,
+                      "warmup": args.warmup, "lse_table": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -420,6 +460,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-points", type=int, default=2048)
+    ap.add_argument("--lse-table", action="store_true",
+                    help="row-sweep timings at the paper's Table 1 sizes (n = 1024 .. 65536) instead of the bench")
     args = ap.parse_args()
     args.ttt = not args.no_ttt
     if args.prec is None:
@@ -428,7 +470,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.warmup < 3 and args.impl == "gpu":
         raise SystemExit("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.lse_table:
+        run_lse_table(args)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_gpu(args, rank, world)

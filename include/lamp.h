@@ -177,7 +177,9 @@ LAMP_API int lamp_objective(lamp_ctx* ctx, double out[8]);
  * 1 <= k <= 8 value columns (colour channels, coordinates: p y is the barycentric map).
  * One evaluation pass, then one recompute sweep of X^t over all n m entries with
  * float32 exponents as in the iteration and float64 accumulation across tiles.
- * Asynchronous on the context's stream after the evaluation pass. */
+ * The first call with k larger than the context's partial-sum width (3, or d for
+ * |x - y|^2 with d <= 8) widens two O(k (n + m) splits) buffers (LAMP_E_NOMEM if that
+ * fails).  Asynchronous on the context's stream after the evaluation pass. */
 LAMP_API int lamp_apply_map(lamp_ctx* ctx, const float* V, int64_t k, float* out, int side);
 
 /* Dual function of the saddle problem (App. B, Eqs. def:dual_spp, def:dual_spp_e)

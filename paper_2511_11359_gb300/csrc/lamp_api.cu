@@ -28,6 +28,7 @@ struct lamp_ctx {
   double Hr = 0.0;             // entropy of r
   double log_m = 0.0;
   int rowblocks = 0;
+  int part_width = 3;  // values per point the partial-sum buffers hold (per split)
   std::vector<void*> allocs;
   // owned input copies (lamp_create_owned)
   bool owned = false;
@@ -264,7 +265,8 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
   k.cost_op = prob->kind == LAMP_COST_L1 ? 1 : prob->kind == LAMP_COST_LINF ? 2 : 0;
   // direct-form cost (z = |x - y|^2) for small d; dot form x.y above (|x - y|^2 only)
   k.zdot = (pts && k.cost_op == 0 && (prob->d > 8 || params->prec == LAMP_PREC_BF16_TC)) ? 1 : 0;
-  k.shared_shift = uses_direct_sweeps(k, params->prec) ? 1 : 0;
+  // the packed sweeps (direct form and tensor cores) derive stream B from stream A
+  k.shared_shift = (uses_direct_sweeps(k, params->prec) || params->prec == LAMP_PREC_BF16_TC) ? 1 : 0;
   k.eta = params->eta;
   k.alpha = params->alpha;
   k.clipb = std::tanh(params->beta / 2.0);
@@ -333,7 +335,9 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
     int64_t tci = (k.n + tile_inner_cols(k, ctx->prec) - 1) / tile_inner_cols(k, ctx->prec);
     g.rows_tiles = (int)to;
     g.cols_tiles = (int)tco;
-    int min_inner = k.kind == LAMP_COST_DENSE ? 1 : 4;
+    // at least 4 inner tiles per CTA (dense rows: 2 chunks of 1024 columns), so that a
+    // CTA's fixed costs (parameters, reduction) stay small against its sweep
+    int min_inner = k.kind == LAMP_COST_DENSE ? 2 : 4;
     g.rows_split = choose_split(to, ti, (int64_t)g.sms * bpr, min_inner);
     g.cols_split = choose_split(tco, tci, (int64_t)g.sms * bpc, k.kind == LAMP_COST_DENSE ? 4 : min_inner);
   }
@@ -343,8 +347,10 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
   const size_t n = (size_t)k.n, m = (size_t)k.m;
   ctx->rowblocks = (int)fin_blocks(k.n);
   int colblocks = (int)fin_blocks(k.m);
-  // partial sums of the gradient (d values per point) and of the transport map (up to 8)
-  const size_t gradd = 8;
+  // partial-sum width: the sweeps' 2 / 3 values per point, and the gradient's d values;
+  // the transport map widens the buffers on first use (ensure_part_width)
+  const size_t gradd = k.kind == COST_SQEUCLID ? (size_t)std::min<int64_t>(std::max<int64_t>(k.d, 2), 8) : 2;
+  ctx->part_width = (int)std::max<size_t>(3, gradd);
   // column / row data are padded to 128-entry multiples (padding entries contribute nothing)
   const size_t m_pad = (size_t)tc_pad(k.m), n_pad = (size_t)tc_pad(k.n);
   for (int b = 0; b < 2; ++b) {
@@ -359,8 +365,8 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
       if ((rc = dalloc(ctx, &w.colq2[b], m_pad))) return bail(rc);
     if ((rc = dalloc(ctx, &w.g2row2, n_pad))) return bail(rc);
   }
-  if ((rc = dalloc(ctx, &w.rowpart, (size_t)g.rows_split * std::max<size_t>(2, gradd) * n))) return bail(rc);
-  if ((rc = dalloc(ctx, &w.colpart, (size_t)g.cols_split * std::max<size_t>(3, gradd) * m))) return bail(rc);
+  if ((rc = dalloc(ctx, &w.rowpart, (size_t)g.rows_split * ctx->part_width * n))) return bail(rc);
+  if ((rc = dalloc(ctx, &w.colpart, (size_t)g.cols_split * ctx->part_width * m))) return bail(rc);
   if ((rc = dalloc(ctx, &w.logZ, n))) return bail(rc);
   if ((rc = dalloc(ctx, &w.colA, m))) return bail(rc);
   if ((rc = dalloc(ctx, &w.colz, m))) return bail(rc);
@@ -657,12 +663,37 @@ static int end_passes(lamp_ctx* ctx) {
   return LAMP_OK;
 }
 
+// widen rowpart / colpart to `width` values per point (per split); the captured graphs hold
+// the old pointers, so they are dropped and rebuilt on their next use
+static int ensure_part_width(lamp_ctx* ctx, int width) {
+  if (width <= ctx->part_width) return LAMP_OK;
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (double* old : {ctx->w.rowpart, ctx->w.colpart}) {
+    auto it = std::find(ctx->allocs.begin(), ctx->allocs.end(), (void*)old);
+    if (it != ctx->allocs.end()) ctx->allocs.erase(it);
+    cudaFree(old);
+  }
+  ctx->w.rowpart = ctx->w.colpart = nullptr;
+  for (int s = 0; s < 3; ++s) {
+    if (ctx->gexec[s]) cudaGraphExecDestroy(ctx->gexec[s]);
+    ctx->gexec[s] = nullptr;
+    ctx->glen[s] = 0;
+  }
+  int rc = dalloc(ctx, &ctx->w.rowpart, (size_t)ctx->g.rows_split * width * ctx->k.n);
+  if (!rc) rc = dalloc(ctx, &ctx->w.colpart, (size_t)ctx->g.cols_split * width * ctx->k.m);
+  if (rc) return rc;
+  ctx->part_width = width;
+  return LAMP_OK;
+}
+
 extern "C" int lamp_apply_map(lamp_ctx* ctx, const float* V, int64_t k, float* out, int side) {
   if (!ctx || !V || !out) return fail(ctx, LAMP_E_INVALID, "lamp_apply_map: null argument");
   if (k < 1 || k > 8) return fail(ctx, LAMP_E_INVALID, "lamp_apply_map: 1 <= k <= 8 value columns (got %lld)",
                                   (long long)k);
   if (side != 0 && side != 1) return fail(ctx, LAMP_E_INVALID, "lamp_apply_map: side must be 0 (p V) or 1 (p^T U)");
-  int rc = evaluate(ctx);
+  int rc = ensure_part_width(ctx, (int)k);
+  if (rc) return rc;
+  rc = evaluate(ctx);
   if (rc) return rc;
   CK(launch_map(ctx->in, ctx->k, ctx->w, ctx->g, ctx->host_dev->cur, V, (int)k, out, side, ctx->stream));
   return LAMP_OK;

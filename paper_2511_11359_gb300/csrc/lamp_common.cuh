@@ -94,19 +94,6 @@ __host__ __device__ inline double kappa_next(double kap, const Consts& k) {
   return k.tau1 + kap * (1.0 - k.tau1 * k.eta);
 }
 
-__host__ __device__ inline double pow2i(int e) {
-  // exact 2^e for |e| < 1000
-  double r = 1.0;
-  double b = e >= 0 ? 2.0 : 0.5;
-  int q = e >= 0 ? e : -e;
-  while (q) {
-    if (q & 1) r *= b;
-    b *= b;
-    q >>= 1;
-  }
-  return r;
-}
-
 // kappa of the sweeps: the state's, unless an evaluation pass overrides it
 __host__ __device__ inline double sweep_kappa(double dev_kappa, const Consts& k) {
   return k.kap_ovr >= 0.0 ? k.kap_ovr : dev_kappa;
@@ -131,11 +118,11 @@ __host__ __device__ inline SweepParams make_sweep_params(double kap, const Const
   p.alB = (float)(p.aB - (double)p.ahB);
   double lmax = p.lamA > p.lamB ? p.lamA : p.lamB;
   double bound = lmax * k.W + 128.0;
-  // smallest e with 2^e >= bound, then g = 2^(e-23)
-  int e = 0;
-  double v = 1.0;
-  while (v < bound) { v *= 2.0; ++e; }
-  p.g = pow2i(e - 23);
+  // smallest e with 2^e >= bound (bound = f 2^ex, f in [0.5, 1)), then g = 2^(e-23)
+  int ex;
+  const double f = frexp(bound, &ex);
+  const int e = f == 0.5 ? ex - 1 : ex;
+  p.g = ldexp(1.0, e - 23);
   return p;
 }
 
@@ -151,14 +138,15 @@ __host__ __device__ inline double quantize(double x, double g) {
 }
 
 #ifdef __CUDACC__
-// write entry e of a packed-pair array (layout described in Work)
+// write entry e of a packed-pair array (layout described in Work); offA - offB is a
+// difference of two grid multiples, exact in float32 (see the top of this file)
 __device__ __forceinline__ void store_pair_entry(float4* __restrict__ a, int64_t e, float offA, float wA, float offB,
                                                  float wB) {
   float* fa = reinterpret_cast<float*>(a + (e >> 1) * 2);
   const int h = (int)(e & 1);
   fa[0 + h] = -offA;
   fa[2 + h] = wA;
-  fa[4 + h] = -offB;
+  fa[4 + h] = offA - offB;
   fa[6 + h] = wB;
 }
 
@@ -262,9 +250,11 @@ struct Work {
   float4* colq[2];     // per column {BqA, wA, BqB, wB}
   float2* rowshift[2]; // per row {RqA, RqB}
   float4* g2row;       // per row {RqA, qA, RqB, qB} for the column sweep
-  // the same data in the packed-pair layout read by the tensor-core sweeps (null when
-  // unused): for entries 2p, 2p+1 two float4, [2p] = {-offA_2p, -offA_2p+1, wgtA_2p,
-  // wgtA_2p+1} and [2p+1] = the same for stream B; padding halves hold {-2^100, 0}
+  // the same data in the packed-pair layout read by the packed sweeps (null when unused):
+  // for entries 2p, 2p+1 two float4, [2p] = {-offA_2p, -offA_2p+1, wgtA_2p, wgtA_2p+1}
+  // and [2p+1] = {offA_2p - offB_2p, offA_2p+1 - offB_2p+1, wgtB_2p, wgtB_2p+1} (the
+  // offset difference that stream B adds to stream A's exponent under the shared row
+  // shift); padding halves hold {-2^100, 0}
   float4* colq2[2];
   float4* g2row2;
   double* rowpart;     // [splits_rows][2][n] partial row sums
@@ -329,8 +319,9 @@ cudaError_t tc_prepare();
 // self-test of the bounded mbarrier wait (0, or a LAMP_E_* code); *status = the device status word
 int tc_wait_selftest(uint32_t polls, int* status);
 int tc_blocks_per_sm(int which);
-cudaError_t tc_launch_sweep(bool rows, const void* map_x, const void* map_y, const Work& w, const Consts& k,
-                            int splits, cudaStream_t st);
+// eval = 1: the column sweep of an evaluation pass (with the cost-weighted sums)
+cudaError_t tc_launch_sweep(bool rows, int eval, const void* map_x, const void* map_y, const Work& w,
+                            const Consts& k, int splits, cudaStream_t st);
 cudaError_t launch_iteration_part(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
                                   int part, int eval, cudaStream_t st);
 int tile_outer_cols(const Consts& k, int prec);

@@ -186,9 +186,8 @@ k_pts_direct(const float* __restrict__ P_out, const float* __restrict__ P_in, in
         const float4 dB = *reinterpret_cast<const float4*>(rp + 2 * DP + 4);
         const uint64_t oA2 = pk(dA.x, dA.y), wA2 = pk(dA.z, dA.w);
         const uint64_t wB2 = pk(dB.z, dB.w);
-        // row sweep: the inner columns' BqA_j - BqB_j (exact, as for ownD)
-        uint64_t dC2 = 0ull;
-        if constexpr (MODE == M_ROWSUM) dC2 = f2sub(pk(dB.x, dB.y), oA2);
+        // row sweep: the inner columns' BqA_j - BqB_j (stored exactly in the pair data)
+        const uint64_t dC2 = pk(dB.x, dB.y);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           uint64_t z2;

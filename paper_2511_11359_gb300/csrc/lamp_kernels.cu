@@ -993,13 +993,13 @@ cudaError_t launch_iteration_part(const Inputs& in, const Consts& k, const Work&
   const bool tcpath = prec == 1 /* LAMP_PREC_BF16_TC */;
   switch (part) {
     case 0:
-      if (tcpath) return tc_launch_sweep(true, g.map_x, g.map_y, w, k, g.rows_split, st);
+      if (tcpath) return tc_launch_sweep(true, 0, g.map_x, g.map_y, w, k, g.rows_split, st);
       return launch_row_sweep(in, k, w, g, M_ROWSUM, st);
     case 1:
       k_row_fin<<<rb, kFinThreads, 0, st>>>(w, g.rows_split, in.r, k);
       return cudaGetLastError();
     case 2:
-      if (tcpath) return tc_launch_sweep(false, g.map_x, g.map_y, w, k, g.cols_split, st);
+      if (tcpath) return tc_launch_sweep(false, eval, g.map_x, g.map_y, w, k, g.cols_split, st);
       return launch_col_sweep(in, k, w, g, eval, st);
     default:
       // the packed direct-form column sweep accumulates <C, X> in evaluation passes only

@@ -227,7 +227,8 @@ __host__ __device__ constexpr uint32_t idesc_bf16_128x128() {
 // ROWS = true: G1 (fixed x tile, streamed y tiles, per-row sums of both streams)
 // ROWS = false: G2 (fixed y tile, streamed x tiles, per-column sums of both streams
 // and of z X for <C, X>)
-template <bool ROWS>
+// WC: column sweep of an evaluation pass (also accumulates sum_i z_ij X_ij for <C, X^t>)
+template <bool ROWS, int WC>
 __global__ void __launch_bounds__(kThreads, 2)
 k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_y, const Work w,
            int64_t n, int64_t m, int tiles_per_split, const Consts k) {
@@ -341,46 +342,58 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
     const int h = warp >> 2;               // which 64 of the 128 accumulator columns
     const SweepParams sp = make_sweep_params(sweep_kappa(dev->kappa, k), k);
     const uint64_t ahA2 = pk(sp.ahA, sp.ahA), alA2 = pk(sp.alA, sp.alA);
-    const uint64_t ahB2 = pk(sp.ahB, sp.ahB), alB2 = pk(sp.alB, sp.alB);
+    const float dal = (float)(sp.aB - sp.aA);  // stream B: v^B = (a^B - a^A) z + (v^A + dB)
+    const uint64_t da2 = pk(dal, dal);
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;  // TMEM lane field
-    // this thread's own offsets (G1: its row's shifts; G2: its column's offsets), negated
-    uint64_t ownA2, ownB2;
+    // this thread's own offsets (G1: its row's shift; G2: its column's offset and the
+    // column's BqA - BqB), negated / as stored in the pair arrays
+    uint64_t ownA2, ownD2 = 0ull;
     const int64_t own = fixed0 + t;
     if (ROWS) {
       const float2 rq = w.rowshift[cur][own < n ? own : n - 1];
       ownA2 = pk(-rq.x, -rq.x);
-      ownB2 = pk(-rq.y, -rq.y);
     } else {
       const float4 cq = w.colq[cur][own];  // padded columns: {+inf, 0, +inf, 0}
       ownA2 = pk(-cq.x, -cq.x);
-      ownB2 = pk(-cq.z, -cq.z);
+      const float db = isfinite(cq.x) ? cq.x - cq.z : 0.f;  // exact (grid multiples)
+      ownD2 = pk(db, db);
     }
     float hiA = 0.f, loA = 0.f, hiB = 0.f, loB = 0.f, hiC = 0.f, loC = 0.f;
-    // process 16 accumulator columns (8 pairs) starting at column col of the tile
+    // packed pair sums over this warp's 64 columns of a tile (two alternating accumulators)
+    uint64_t accA[2], accB[2], accC[2];
+    auto reset = [&]() {
+      accA[0] = accA[1] = accB[0] = accB[1] = accC[0] = accC[1] = 0ull;
+    };
+    auto fold = [&]() {
+      const float2 a2 = upk(f2add(accA[0], accA[1])), b2 = upk(f2add(accB[0], accB[1]));
+      ff_add(hiA, loA, a2.x + a2.y);
+      ff_add(hiB, loB, b2.x + b2.y);
+      if (WC) {
+        const float2 c2 = upk(f2add(accC[0], accC[1]));
+        ff_add(hiC, loC, c2.x + c2.y);
+      }
+    };
+    // 16 accumulator columns (8 pairs) starting at column col of the tile
     auto half_chunk = [&](const uint32_t (&v)[16], const float4* pr, int col) {
-      uint64_t accA[2] = {0ull, 0ull}, accB[2] = {0ull, 0ull}, accC[2] = {0ull, 0ull};
 #pragma unroll
       for (int p = 0; p < 8; ++p) {
         const float4 qa = pr[col + 2 * p];
         const float4 qb = pr[col + 2 * p + 1];
         const uint64_t z2 = pk(__uint_as_float(v[2 * p]), __uint_as_float(v[2 * p + 1]));
-        const uint64_t eA = exp2_pair(ahA2, alA2, z2, f2add(ownA2, pk(qa.x, qa.y)));
-        const uint64_t eB = exp2_pair(ahB2, alB2, z2, f2add(ownB2, pk(qb.x, qb.y)));
-        if (ROWS) {
-          accA[p & 1] = f2fma(eA, pk(qa.z, qa.w), accA[p & 1]);
-        } else {
+        const uint64_t vA = f2fma(alA2, z2, f2fma(ahA2, z2, f2add(ownA2, pk(qa.x, qa.y))));
+        // G1: the inner column's BqA - BqB from the pair data; G2: the own column's
+        const uint64_t vB = f2fma(da2, z2, f2add(vA, ROWS ? pk(qb.x, qb.y) : ownD2));
+        const float2 vAf = upk(vA), vBf = upk(vB);
+        const uint64_t eA = pk(ex2(vAf.x), ex2(vAf.y));
+        const uint64_t eB = pk(ex2(vBf.x), ex2(vBf.y));
+        if (WC) {
           const uint64_t pA = f2mul(eA, pk(qa.z, qa.w));
           accA[p & 1] = f2add(accA[p & 1], pA);
           accC[p & 1] = f2fma(z2, pA, accC[p & 1]);
+        } else {
+          accA[p & 1] = f2fma(eA, pk(qa.z, qa.w), accA[p & 1]);
         }
         accB[p & 1] = f2fma(eB, pk(qb.z, qb.w), accB[p & 1]);
-      }
-      const float2 a2 = upk(f2add(accA[0], accA[1])), b2 = upk(f2add(accB[0], accB[1]));
-      ff_add(hiA, loA, a2.x + a2.y);
-      ff_add(hiB, loB, b2.x + b2.y);
-      if (!ROWS) {
-        const float2 c2 = upk(f2add(accC[0], accC[1]));
-        ff_add(hiC, loC, c2.x + c2.y);
       }
     };
     for (int i = 0; i < ntiles; ++i) {
@@ -394,6 +407,7 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
       // this warp's 64 columns as two 32-column loads (each with its wait); other warps
       // of the SM sub-partition cover the TMEM latency
       const uint32_t tbase = tmem + lane_base + b * kTile + h * 64;
+      reset();
 #pragma unroll 1
       for (int c = 0; c < 2; ++c) {
         uint32_t v[32];
@@ -401,6 +415,7 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
         half_chunk(*reinterpret_cast<const uint32_t(*)[16]>(&v[0]), pr, h * 64 + c * 32);
         half_chunk(*reinterpret_cast<const uint32_t(*)[16]>(&v[16]), pr, h * 64 + c * 32 + 16);
       }
+      fold();
       tc_fence_before();
       mbar_arrive(&B->tmem_empty[b]);
       mbar_arrive(&B->pair_empty[b]);
@@ -424,9 +439,10 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
           w.rowpart[((int64_t)blockIdx.y * 2 + 1) * n + own] = sB;
         }
       } else if (own < m) {
-        w.colpart[((int64_t)blockIdx.y * 3 + 0) * m + own] = sA;
-        w.colpart[((int64_t)blockIdx.y * 3 + 1) * m + own] = sB;
-        w.colpart[((int64_t)blockIdx.y * 3 + 2) * m + own] = sC;
+        constexpr int na = WC ? 3 : 2;  // the layout k_col_fin reads for this pass
+        w.colpart[((int64_t)blockIdx.y * na + 0) * m + own] = sA;
+        w.colpart[((int64_t)blockIdx.y * na + 1) * m + own] = sB;
+        if (WC) w.colpart[((int64_t)blockIdx.y * na + 2) * m + own] = sC;
       }
     }
   }
@@ -551,26 +567,28 @@ cudaError_t tc_make_map(void* map_out, const void* base, int64_t rows_pad) {
 }
 
 cudaError_t tc_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(tc::k_tc_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)tc_smem_bytes());
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(tc::k_tc_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)tc_smem_bytes());
+  const int sm = (int)tc_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(tc::k_tc_sweep<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc::k_tc_sweep<false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc::k_tc_sweep<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  return e;
 }
 
 int tc_blocks_per_sm(int which) {
   int nb = 0;
   if (which == 0)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tc::k_tc_sweep<true>, tc::kThreads, tc_smem_bytes());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tc::k_tc_sweep<true, 0>, tc::kThreads, tc_smem_bytes());
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tc::k_tc_sweep<false>, tc::kThreads, tc_smem_bytes());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tc::k_tc_sweep<false, 1>, tc::kThreads, tc_smem_bytes());
   // two 256-column TMEM allocations fill the 512 columns of an SM
   if (nb > 2) nb = 2;
   return nb > 0 ? nb : 1;
 }
 
-cudaError_t tc_launch_sweep(bool rows, const void* map_x, const void* map_y, const Work& w, const Consts& k,
-                            int splits, cudaStream_t st) {
+cudaError_t tc_launch_sweep(bool rows, int eval, const void* map_x, const void* map_y, const Work& w,
+                            const Consts& k, int splits, cudaStream_t st) {
   const int64_t nfixed = rows ? k.n : k.m;
   const int64_t nstream = rows ? k.m : k.n;
   const int64_t ntiles = (nstream + tc::kTile - 1) / tc::kTile;
@@ -579,9 +597,11 @@ cudaError_t tc_launch_sweep(bool rows, const void* map_x, const void* map_y, con
   const CUtensorMap& mx = *reinterpret_cast<const CUtensorMap*>(map_x);
   const CUtensorMap& my = *reinterpret_cast<const CUtensorMap*>(map_y);
   if (rows)
-    tc::k_tc_sweep<true><<<grid, tc::kThreads, tc_smem_bytes(), st>>>(mx, my, w, k.n, k.m, tps, k);
+    tc::k_tc_sweep<true, 0><<<grid, tc::kThreads, tc_smem_bytes(), st>>>(mx, my, w, k.n, k.m, tps, k);
+  else if (eval)
+    tc::k_tc_sweep<false, 1><<<grid, tc::kThreads, tc_smem_bytes(), st>>>(mx, my, w, k.n, k.m, tps, k);
   else
-    tc::k_tc_sweep<false><<<grid, tc::kThreads, tc_smem_bytes(), st>>>(mx, my, w, k.n, k.m, tps, k);
+    tc::k_tc_sweep<false, 0><<<grid, tc::kThreads, tc_smem_bytes(), st>>>(mx, my, w, k.n, k.m, tps, k);
   return cudaGetLastError();
 }
 
