@@ -238,11 +238,11 @@ LAMP_API int lamp_step_host(lamp_ctx* ctx, const float* C_or_x, const float* y, 
  * inputs; prob's pointers are HOST pointers and are copied once here. */
 LAMP_API int lamp_create_owned(lamp_ctx** out, const lamp_problem* host_prob, const lamp_params* params, void* stream);
 
-/* Apply `iters` iterations (as lamp_iterate) launched one kernel at a time with
- * CUDA events between the kernels on the context's stream, and return the mean
- * device time in milliseconds of each kernel of an iteration in ms_out[0..3]:
- * [0] row sweep, [1] row finalize, [2] column sweep, [3] column finalize.
- * Synchronises.  iters >= 1. */
+/* Apply iters + 1 iterations (as lamp_iterate) launched one kernel at a time, the
+ * last `iters` of them with CUDA events between consecutive kernels on the context's
+ * stream and one synchronisation at the end, and return the mean device time in
+ * milliseconds of each kernel of an iteration in ms_out[0..3]: [0] row sweep, [1] row
+ * finalize, [2] column sweep, [3] column finalize.  Synchronises.  1 <= iters <= 1000. */
 LAMP_API int lamp_time_kernels(lamp_ctx* ctx, int64_t iters, double* ms_out);
 
 /* Measurement helper with no counterpart in the paper: the sustained MUFU ex2

@@ -875,36 +875,44 @@ extern "C" int lamp_step_host(lamp_ctx* ctx, const float* C_or_x, const float* y
 
 extern "C" int lamp_time_kernels(lamp_ctx* ctx, int64_t iters, double* ms_out) {
   if (!ctx || !ms_out) return fail(ctx, LAMP_E_INVALID, "lamp_time_kernels: null argument");
-  if (iters < 1) return fail(ctx, LAMP_E_INVALID, "iters must be >= 1");
-  k_ctrl<<<1, 1, 0, ctx->stream>>>(ctx->w.dev, 0, -1.0, 0, iters, 0);
+  if (iters < 1 || iters > 1000) return fail(ctx, LAMP_E_INVALID, "iters must be in [1, 1000]");
+  k_ctrl<<<1, 1, 0, ctx->stream>>>(ctx->w.dev, 0, -1.0, 0, iters + 1, 0);
   CK(cudaGetLastError());
-  cudaEvent_t ev[5];
-  for (int i = 0; i < 5; ++i) CK(cudaEventCreate(&ev[i]));
-  double acc[4] = {0, 0, 0, 0};
+  // one untimed iteration first, then all timed launches back to back with an event
+  // between consecutive kernels; a single synchronisation at the end, so no launch
+  // latency of an idle stream falls inside a kernel's interval
+  std::vector<cudaEvent_t> ev((size_t)(4 * iters + 1), nullptr);
   int rc = LAMP_OK;
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) rc = fail(ctx, LAMP_E_CUDA, "cudaEventCreate failed");
+  for (int part = 0; part < 4 && rc == LAMP_OK; ++part) {
+    cudaError_t e = launch_iteration_part(ctx->in, ctx->k, ctx->w, ctx->g, ctx->prec, part, 0, ctx->stream);
+    if (e != cudaSuccess) rc = fail(ctx, LAMP_E_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+  }
+  if (rc == LAMP_OK) cudaEventRecord(ev[0], ctx->stream);
   for (int64_t it = 0; it < iters && rc == LAMP_OK; ++it) {
-    cudaEventRecord(ev[0], ctx->stream);
     for (int part = 0; part < 4; ++part) {
       cudaError_t e = launch_iteration_part(ctx->in, ctx->k, ctx->w, ctx->g, ctx->prec, part, 0, ctx->stream);
       if (e != cudaSuccess) {
         rc = fail(ctx, LAMP_E_CUDA, "kernel launch: %s", cudaGetErrorString(e));
         break;
       }
-      cudaEventRecord(ev[part + 1], ctx->stream);
-    }
-    if (rc) break;
-    cudaError_t e = cudaEventSynchronize(ev[4]);
-    if (e != cudaSuccess) {
-      rc = fail(ctx, LAMP_E_CUDA, "cudaEventSynchronize: %s", cudaGetErrorString(e));
-      break;
-    }
-    for (int part = 0; part < 4; ++part) {
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, ev[part], ev[part + 1]);
-      acc[part] += ms;
+      cudaEventRecord(ev[(size_t)(4 * it + part + 1)], ctx->stream);
     }
   }
-  for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+  double acc[4] = {0, 0, 0, 0};
+  if (rc == LAMP_OK) {
+    cudaError_t e = cudaEventSynchronize(ev.back());
+    if (e != cudaSuccess) rc = fail(ctx, LAMP_E_CUDA, "cudaEventSynchronize: %s", cudaGetErrorString(e));
+  }
+  for (int64_t it = 0; it < iters && rc == LAMP_OK; ++it)
+    for (int part = 0; part < 4; ++part) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[(size_t)(4 * it + part)], ev[(size_t)(4 * it + part + 1)]);
+      acc[part] += ms;
+    }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
   if (rc) return rc;
   for (int part = 0; part < 4; ++part) ms_out[part] = acc[part] / (double)iters;
   return LAMP_OK;

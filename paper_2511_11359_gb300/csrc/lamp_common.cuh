@@ -30,12 +30,14 @@
 // The sub-grid remainder Br_j = Bcol_j - Bq_j enters as the factor
 // w_j = 2^{-Br_j} (row sums) or as a per-column factor after the sum (column sums).
 //
-// Shared row shift (packed direct-form sweeps, Consts::shared_shift): stream B
-// uses stream A's row shift, RqB_i = RqA_i, and its exponent is derived from
-// stream A's as v^B = (a^B - a^A) z + (v^A + (BqA_j - BqB_j)).  BqA_j - BqB_j is
-// a difference of two grid multiples, hence exact, and O(1): kappa_{t+1} nubar_j
-// and kappa_t nu_j differ by O(tau1), so v^B - v^A = O(1) for every entry and
-// the row sums of stream B stay within a few powers of two of 1.
+// Shared row shift (packed sweeps, Consts::shared_shift): stream B uses stream A's
+// row shift, RqB_i = RqA_i, and its exponent is derived from stream A's as
+// v^B = (a^B - a^A) z + (v^A + dB_j) with dB_j = BqA_j - BcolB_j (BcolB unquantised,
+// so the column weight of stream B is inside the exponent).  dB_j is O(1):
+// kappa_{t+1} nubar_j and kappa_t nu_j differ by O(tau1), so v^B - v^A = O(1) for
+// every entry, the row sums of stream B stay within a few powers of two of 1, and
+// the rounding of v^A + dB_j is relative to O(1) numbers.  The row sweep then sums
+// 2^{v^B} with no weight, and the column finalize takes stream B's column sum as is.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -138,16 +140,20 @@ __host__ __device__ inline double quantize(double x, double g) {
 }
 
 #ifdef __CUDACC__
-// write entry e of a packed-pair array (layout described in Work); offA - offB is a
-// difference of two grid multiples, exact in float32 (see the top of this file)
-__device__ __forceinline__ void store_pair_entry(float4* __restrict__ a, int64_t e, float offA, float wA, float offB,
+// write entry e of a packed-pair array (layout described in Work)
+__device__ __forceinline__ void store_pair_entry(float4* __restrict__ a, int64_t e, float offA, float wA, float dB,
                                                  float wB) {
   float* fa = reinterpret_cast<float*>(a + (e >> 1) * 2);
   const int h = (int)(e & 1);
   fa[0 + h] = -offA;
   fa[2 + h] = wA;
-  fa[4 + h] = offA - offB;
+  fa[4 + h] = dB;
   fa[6 + h] = wB;
+}
+
+// stream B's term of entry e of a column pair array: dB_e = BqA_e - BcolB_e
+__device__ __forceinline__ float pair_dB(const float4* __restrict__ a, int64_t e) {
+  return reinterpret_cast<const float*>(a + (e >> 1) * 2 + 1)[e & 1];
 }
 
 // 2^x with the SFU (MUFU.EX2), flush-to-zero
@@ -196,13 +202,15 @@ __device__ __forceinline__ uint64_t exp2_pair(uint64_t ah2, uint64_t al2, uint64
 }
 
 // the column data {BqA, wA, BqB, wB} of one column for sweep parameters sp: Bcol of
-// each stream rounded to the grid, and the factor 2^{-remainder}
+// each stream rounded to the grid, and the factor 2^{-remainder}; *dB (if given) gets
+// BqA - BcolB, stream B's term under the shared row shift (see the top of this file)
 __device__ __forceinline__ float4 column_data(double nu_j, double nubar_j, double sny_j, const SweepParams& sp,
-                                              const Consts& k) {
+                                              const Consts& k, float* dB = nullptr) {
   double bA = sp.lamA * (sny_j + 2.0 * k.K * nu_j);
   double bB = sp.lamB * (sny_j + 2.0 * k.K * nubar_j);
   double qA = quantize(bA, sp.g);
   double qB = quantize(bB, sp.g);
+  if (dB) *dB = (float)(qA - bB);
   return make_float4((float)qA, (float)exp2(-(bA - qA)), (float)qB, (float)exp2(-(bB - qB)));
 }
 
@@ -252,9 +260,9 @@ struct Work {
   float4* g2row;       // per row {RqA, qA, RqB, qB} for the column sweep
   // the same data in the packed-pair layout read by the packed sweeps (null when unused):
   // for entries 2p, 2p+1 two float4, [2p] = {-offA_2p, -offA_2p+1, wgtA_2p, wgtA_2p+1}
-  // and [2p+1] = {offA_2p - offB_2p, offA_2p+1 - offB_2p+1, wgtB_2p, wgtB_2p+1} (the
-  // offset difference that stream B adds to stream A's exponent under the shared row
-  // shift); padding halves hold {-2^100, 0}
+  // and [2p+1] = {dB_2p, dB_2p+1, wgtB_2p, wgtB_2p+1}: columns dB = BqA - BcolB, the
+  // term stream B adds to stream A's exponent under the shared row shift; rows dB = 0
+  // (unused); padding halves hold {-2^100, 0}
   float4* colq2[2];
   float4* g2row2;
   double* rowpart;     // [splits_rows][2][n] partial row sums

@@ -28,7 +28,8 @@ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // entries (outer, 2p) and (outer, 2p + 1).  Per pair of entries: d subtractions
 // and d multiply-adds for z = |x - y|^2; stream A one add, two fma (compensated
 // exponent), two ex2 and one fma (weighted sum); stream B, through the shared row
-// shift (see lamp_common.cuh), one add, one fma, two ex2 and one fma.  Evaluation
+// shift (see lamp_common.cuh), one add, one fma, two ex2 and one add (row sums) or
+// fma (column sums).  Evaluation
 // passes also accumulate sum_i z_ij X_ij in the column sweep (two more).
 // z = sum_k (x_k - y_k)^2 is accumulated in the same k order in both sweeps, and
 // (y - x)^2 == (x - y)^2 in IEEE arithmetic, so the row and the column sweep see
@@ -137,18 +138,14 @@ k_pts_direct(const float* __restrict__ P_out, const float* __restrict__ P_in, in
       const float v = P_out[go * D + kk];
       x2[r][kk] = pk(v, v);
     }
-    float qa, qb;
+    float qa, db = 0.f;
     if (MODE == M_ROWSUM) {
-      const float2 q = w.rowshift[cur][go];
-      qa = q.x;
-      qb = q.y;
+      qa = w.rowshift[cur][go].x;
     } else {
-      const float4 q = w.colq[cur][go];
-      qa = q.x;
-      qb = q.z;
+      qa = w.colq[cur][go].x;
+      db = pair_dB(w.colq2[cur], go);  // the same float the row sweep reads for this column
     }
     ownA[r] = pk(-qa, -qa);
-    const float db = (-qb) - (-qa);  // exact: two multiples of the grid (see lamp_common.cuh)
     ownD[r] = pk(db, db);
   }
 
@@ -186,7 +183,7 @@ k_pts_direct(const float* __restrict__ P_out, const float* __restrict__ P_in, in
         const float4 dB = *reinterpret_cast<const float4*>(rp + 2 * DP + 4);
         const uint64_t oA2 = pk(dA.x, dA.y), wA2 = pk(dA.z, dA.w);
         const uint64_t wB2 = pk(dB.z, dB.w);
-        // row sweep: the inner columns' BqA_j - BqB_j (stored exactly in the pair data)
+        // row sweep: the inner columns' dB_j = BqA_j - BcolB_j from the pair data
         const uint64_t dC2 = pk(dB.x, dB.y);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -219,7 +216,9 @@ k_pts_direct(const float* __restrict__ P_out, const float* __restrict__ P_in, in
           } else {
             acc[r][0] = f2fma(eA, wA2, acc[r][0]);
           }
-          acc[r][1] = f2fma(eB, wB2, acc[r][1]);
+          // row sums of stream B carry no weight (it is inside dB_j); column sums weight by q^B_i
+          if constexpr (MODE == M_ROWSUM) acc[r][1] = f2add(acc[r][1], eB);
+          else acc[r][1] = f2fma(eB, wB2, acc[r][1]);
         }
       }
 #pragma unroll

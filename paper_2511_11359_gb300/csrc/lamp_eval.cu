@@ -76,7 +76,8 @@ k_round_cols(const Work w, int cur, const double* __restrict__ c, const float* _
     // weight of the second stream: w_j (1 - y_j) = w_j (A_j - c_j) / A_j
     const float wy = over ? (float)((double)cq.y * ((A - cj) / A)) : 0.0f;
     colq_s[j] = make_float4(cq.x, cq.y, cq.x, wy);
-    if (colq2_s) store_pair_entry(colq2_s, j, cq.x, cq.y, cq.x, wy);
+    // packed sweeps: stream B's term log2(w_j (1 - y_j)) (-inf where y_j = 1: no contribution)
+    if (colq2_s) store_pair_entry(colq2_s, j, cq.x, cq.y, wy > 0.f ? (float)log2((double)wy) : -INFINITY, wy);
     yc = yj * w.colz[j];
     if (k.kind == COST_SQEUCLID) dcn = dc * k.s * w.ny[j];
     if (y_out) y_out[j] = yj;
@@ -227,9 +228,10 @@ k_dual_cols(const Work w, int cur, int which, const double* __restrict__ c, floa
     const double phi = which ? w.nu[cur][j] : w.theta[cur][j];
     const SweepParams sp = make_sweep_params(k.kap_ovr, k);
     const double sny = k.zdot ? k.s * w.ny[j] : 0.0;
-    const float4 cd = column_data(phi, phi, sny, sp, k);
+    float dB;
+    const float4 cd = column_data(phi, phi, sny, sp, k, &dB);
     colq_s[j] = cd;
-    if (colq2_s) store_pair_entry(colq2_s, j, cd.x, cd.y, cd.z, cd.w);
+    if (colq2_s) store_pair_entry(colq2_s, j, cd.x, cd.y, dB, cd.w);
     v = c[j] * phi;
   }
   v = block_sum(v, sh);

@@ -621,9 +621,10 @@ __global__ void k_init_cols(const Work w, const Consts k, int zero) {
   double wt = k.tau1 / sp.kapB;  // tau1 eta_{t+1}
   double nb = nu[j] + wt * (theta[j] - nu[j]);
   double sny = k.zdot ? k.s * ny[j] : 0.0;
-  const float4 cd = column_data(nu[j], nb, sny, sp, k);
+  float dB;
+  const float4 cd = column_data(nu[j], nb, sny, sp, k, &dB);
   colq[j] = cd;
-  if (w.colq2[cur]) store_pair_entry(w.colq2[cur], j, cd.x, cd.y, cd.z, cd.w);
+  if (w.colq2[cur]) store_pair_entry(w.colq2[cur], j, cd.x, cd.y, dB, cd.w);
 }
 
 // row shifts from the prime pass' row maxima: Rq = round_g(max_j (a z_ij - Bq_j))
@@ -685,7 +686,7 @@ k_row_fin(const Work w, int splits, const double* __restrict__ r, const Consts k
     double ri = r[i];
     contrib = ri * lz;
     g2row[i] = make_float4(rq.x, (float)(ri / SA), rq.y, (float)(ri / SB));
-    if (w.g2row2) store_pair_entry(w.g2row2, i, rq.x, (float)(ri / SA), rq.y, (float)(ri / SB));
+    if (w.g2row2) store_pair_entry(w.g2row2, i, rq.x, (float)(ri / SA), 0.f, (float)(ri / SB));
     // shifts of iteration t+1: stream A there has kappa_{t+1} (stream B here);
     // stream B there is extrapolated linearly in t.
     double tA = (double)rq.y + lsB;
@@ -738,7 +739,9 @@ k_col_fin(const Work w, int splits, const double* __restrict__ cvec, int rowbloc
     }
     float4 cq = colq_cur[j];
     const double A = (double)cq.y * aA;  // col(X^t)_j
-    const double B = (double)cq.w * aB;  // col(Xbar^{t+1})_j
+    // col(Xbar^{t+1})_j; under the shared row shift the column weight of stream B is
+    // already inside the sweep's exponents
+    const double B = k.shared_shift ? aB : (double)cq.w * aB;
     const double zsum = (double)cq.y * aC;
     if (!k.zdot) {
       cost = k.s * zsum;
@@ -767,9 +770,10 @@ k_col_fin(const Work w, int splits, const double* __restrict__ cvec, int rowbloc
       const double wn = k.tau1 / spn.kapB;
       const double nbn = nun + wn * (thn - nun);         // nubar^{t+2}
       const double sny = k.zdot ? k.s * ny[j] : 0.0;
-      const float4 cd = column_data(nun, nbn, sny, spn, k);
+      float dB;
+      const float4 cd = column_data(nun, nbn, sny, spn, k, &dB);
       colq_nxt[j] = cd;
-      if (w.colq2[cur ^ 1]) store_pair_entry(w.colq2[cur ^ 1], j, cd.x, cd.y, cd.z, cd.w);
+      if (w.colq2[cur ^ 1]) store_pair_entry(w.colq2[cur ^ 1], j, cd.x, cd.y, dB, cd.w);
     }
   }
   res = warp_sum_d(res);

@@ -345,8 +345,8 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
     const float dal = (float)(sp.aB - sp.aA);  // stream B: v^B = (a^B - a^A) z + (v^A + dB)
     const uint64_t da2 = pk(dal, dal);
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;  // TMEM lane field
-    // this thread's own offsets (G1: its row's shift; G2: its column's offset and the
-    // column's BqA - BqB), negated / as stored in the pair arrays
+    // this thread's own offsets (G1: its row's shift; G2: its column's offset, negated,
+    // and the column's dB as stored in the pair arrays)
     uint64_t ownA2, ownD2 = 0ull;
     const int64_t own = fixed0 + t;
     if (ROWS) {
@@ -355,7 +355,8 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
     } else {
       const float4 cq = w.colq[cur][own];  // padded columns: {+inf, 0, +inf, 0}
       ownA2 = pk(-cq.x, -cq.x);
-      const float db = isfinite(cq.x) ? cq.x - cq.z : 0.f;  // exact (grid multiples)
+      // the column's dB = BqA - BcolB, the same float the row sweep reads (padding: -2^100)
+      const float db = pair_dB(w.colq2[cur], own);
       ownD2 = pk(db, db);
     }
     float hiA = 0.f, loA = 0.f, hiB = 0.f, loB = 0.f, hiC = 0.f, loC = 0.f;
@@ -393,7 +394,9 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
         } else {
           accA[p & 1] = f2fma(eA, pk(qa.z, qa.w), accA[p & 1]);
         }
-        accB[p & 1] = f2fma(eB, pk(qb.z, qb.w), accB[p & 1]);
+        // G1: stream B's column weight is inside dB; G2: weight by the row's q^B
+        if (ROWS) accB[p & 1] = f2add(accB[p & 1], eB);
+        else accB[p & 1] = f2fma(eB, pk(qb.z, qb.w), accB[p & 1]);
       }
     };
     for (int i = 0; i < ntiles; ++i) {
