@@ -52,6 +52,8 @@ struct lamp_ctx {
   float* yr = nullptr;
   alignas(64) unsigned char map_x[128];
   alignas(64) unsigned char map_y[128];
+  alignas(64) unsigned char map_x64[128];
+  alignas(64) unsigned char map_y64[128];
   std::string err;
 };
 
@@ -460,13 +462,17 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
     if ((rc = dalloc(ctx, &ctx->yr, m * (size_t)k.d))) return bail(rc);
     cudaError_t e = tc_convert(in.x, k.n, k.d, ctx->xr, ctx->xb, ctx->stream);
     if (e == cudaSuccess) e = tc_convert(in.y, k.m, k.d, ctx->yr, ctx->yb, ctx->stream);
-    if (e == cudaSuccess) e = tc_make_map(ctx->map_x, ctx->xb, (int64_t)n_pad);
-    if (e == cudaSuccess) e = tc_make_map(ctx->map_y, ctx->yb, (int64_t)m_pad);
+    if (e == cudaSuccess) e = tc_make_map(ctx->map_x, ctx->xb, (int64_t)n_pad, tc_tile_fixed() / 2);
+    if (e == cudaSuccess) e = tc_make_map(ctx->map_y, ctx->yb, (int64_t)m_pad, tc_tile_fixed() / 2);
+    if (e == cudaSuccess) e = tc_make_map(ctx->map_x64, ctx->xb, (int64_t)n_pad, tc_tile_stream());
+    if (e == cudaSuccess) e = tc_make_map(ctx->map_y64, ctx->yb, (int64_t)m_pad, tc_tile_stream());
     if (e != cudaSuccess) return bail(fail(ctx, LAMP_E_CUDA, "bf16 setup: %s", cudaGetErrorString(e)));
     in.x = ctx->xr;
     in.y = ctx->yr;
     g.map_x = ctx->map_x;
     g.map_y = ctx->map_y;
+    g.map_x64 = ctx->map_x64;
+    g.map_y64 = ctx->map_y64;
   }
 
   // cost scale and K = ||C||_inf of the cost the kernels use

@@ -283,8 +283,10 @@ struct Work {
 
 // Launch geometry chosen at create time.
 struct Geometry {
-  const void* map_x;  // tensor maps of the bf16 point copies (LAMP_PREC_BF16_TC), else null
-  const void* map_y;
+  const void* map_x;  // tensor maps of the bf16 point copies (LAMP_PREC_BF16_TC), else null:
+  const void* map_y;  // 128-row boxes (fixed tiles) ...
+  const void* map_x64;  // ... and 64-row boxes (streamed tiles)
+  const void* map_y64;
   int sms;
   int rows_split;   // inner splits of the row sweep
   int cols_split;   // inner splits of the column sweep
@@ -322,14 +324,16 @@ int64_t tc_pad(int64_t v);
 cudaError_t tc_convert(const float* P, int64_t np, int d, float* Pr, void* Pb, cudaStream_t st);
 cudaError_t tc_fill_pads(float4* a, int64_t from, int64_t to, cudaStream_t st);
 cudaError_t tc_fill_pairs(float4* a, int64_t count, cudaStream_t st);
-cudaError_t tc_make_map(void* map_out, const void* base, int64_t rows_pad);
+cudaError_t tc_make_map(void* map_out, const void* base, int64_t rows_pad, int box_rows);
+int tc_tile_fixed();   // points of the fixed tile of a tensor-core sweep
+int tc_tile_stream();  // points of a streamed tile
 cudaError_t tc_prepare();
 // self-test of the bounded mbarrier wait (0, or a LAMP_E_* code); *status = the device status word
 int tc_wait_selftest(uint32_t polls, int* status);
 int tc_blocks_per_sm(int which);
 // eval = 1: the column sweep of an evaluation pass (with the cost-weighted sums)
-cudaError_t tc_launch_sweep(bool rows, int eval, const void* map_x, const void* map_y, const Work& w,
-                            const Consts& k, int splits, cudaStream_t st);
+cudaError_t tc_launch_sweep(bool rows, int eval, const Geometry& g, const Work& w, const Consts& k, int splits,
+                            cudaStream_t st);
 cudaError_t launch_iteration_part(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
                                   int part, int eval, cudaStream_t st);
 int tile_outer_cols(const Consts& k, int prec);

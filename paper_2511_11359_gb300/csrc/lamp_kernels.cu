@@ -997,13 +997,13 @@ cudaError_t launch_iteration_part(const Inputs& in, const Consts& k, const Work&
   const bool tcpath = prec == 1 /* LAMP_PREC_BF16_TC */;
   switch (part) {
     case 0:
-      if (tcpath) return tc_launch_sweep(true, 0, g.map_x, g.map_y, w, k, g.rows_split, st);
+      if (tcpath) return tc_launch_sweep(true, 0, g, w, k, g.rows_split, st);
       return launch_row_sweep(in, k, w, g, M_ROWSUM, st);
     case 1:
       k_row_fin<<<rb, kFinThreads, 0, st>>>(w, g.rows_split, in.r, k);
       return cudaGetLastError();
     case 2:
-      if (tcpath) return tc_launch_sweep(false, eval, g.map_x, g.map_y, w, k, g.cols_split, st);
+      if (tcpath) return tc_launch_sweep(false, eval, g, w, k, g.cols_split, st);
       return launch_col_sweep(in, k, w, g, eval, st);
     default:
       // the packed direct-form column sweep accumulates <C, X> in evaluation passes only
@@ -1067,16 +1067,21 @@ int sweep_blocks_per_sm(const Consts& k, int prec, int which) {
   return nb > 0 ? nb : 1;
 }
 
+// fixed / streamed points per CTA of each sweep (the split choice of lamp_create uses them)
 int tile_outer(const Consts& k, int prec) {
+  if (prec == 1 /* LAMP_PREC_BF16_TC */) return tc_tile_fixed();
   return k.kind == COST_DENSE ? kDR : uses_direct_sweeps(k, prec) ? direct_outer(k.d) : kPT;
 }
 int tile_inner(const Consts& k, int prec) {
+  if (prec == 1) return tc_tile_stream();
   return k.kind == COST_DENSE ? kDChunk : uses_direct_sweeps(k, prec) ? kDirectTile : kPT;
 }
 int tile_outer_cols(const Consts& k, int prec) {
+  if (prec == 1) return tc_tile_fixed();
   return k.kind == COST_DENSE ? kDChunk : uses_direct_sweeps(k, prec) ? direct_outer(k.d) : kPT;
 }
 int tile_inner_cols(const Consts& k, int prec) {
+  if (prec == 1) return tc_tile_stream();
   return k.kind == COST_DENSE ? kDColRows : uses_direct_sweeps(k, prec) ? kDirectTile : kPT;
 }
 

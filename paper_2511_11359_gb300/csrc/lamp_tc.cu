@@ -1,22 +1,25 @@
 // tcgen05 (5th-generation tensor core) sweeps of the LAMP hot path for the
 // squared-Euclidean cost in dot form, BF16 points, FP32 accumulation in TMEM.
 //
-// The row sweep G1 computes, per 128-row x tile (fixed) and 128-column y tile
-// (streamed), D = Xb[rows, 0:64] * Yb[cols, 0:64]^T; the column sweep G2 computes
-// D' = Yb[cols] * Xb[rows]^T with the y tile fixed and x tiles streamed (A and B
-// are 128 x 64 K-major bf16 tiles staged by TMA with 128-byte swizzle).  With
-// bf16 operands every product is exact in fp32 and the MMA's accumulation does
-// not depend on which operand is A: D'[j][i] and D[i][j] are bit-identical, so
-// the column sweep's exponents equal the row sweep's and its normalisation
-// matches the row sums exactly.  In both sweeps one thread owns one TMEM lane
-// (a row of D in G1, a column of X in G2) and accumulates in registers.
+// The row sweep G1 keeps a 256-row x tile fixed (two 128-row halves) and streams
+// 64-row y tiles: per streamed tile two MMAs D_a = Xb[half a, 0:64] * Yb[tile, 0:64]^T
+// (M = 128, N = 64, K = 64).  The column sweep G2 does the same with the roles of x and
+// y exchanged (y tile fixed, x tiles streamed).  Operands are K-major bf16 tiles staged
+// by TMA with 128-byte swizzle.  With bf16 operands every product is exact in fp32 and
+// the MMA's accumulation does not depend on which operand is A: D'[j][i] and D[i][j]
+// are bit-identical, so the column sweep's exponents equal the row sweep's and its
+// normalisation matches the row sums exactly.
 //
-// CTA = 10 warps: warps 0-7 read TMEM (warp w owns lanes 32(w%4).. and columns
-// [64 (w/4), 64 (w/4) + 64) of each 128-column accumulator) and run the exponent /
-// ex2 / accumulation epilogue with packed f32x2 arithmetic over pairs of entries;
-// warp 8 issues TMA loads, warp 9 issues tcgen05.mma.  Two TMEM accumulators (2 x 128 columns)
-// let the MMA of tile i+1 overlap the epilogue of tile i; a 4-stage shared-memory
-// ring feeds the streamed operand.
+// CTA = 10 warps: warps 0-7 read TMEM and run the exponent / ex2 / accumulation
+// epilogue with packed f32x2 arithmetic over pairs of entries; warp w owns TMEM lanes
+// 32 (w % 4) .. + 31 of both accumulator halves, i.e. two rows of D per thread (G1: rows
+// t and 128 + t of the fixed tile; G2: two columns of X), and columns
+// [32 (w / 4), + 32) of each streamed tile.  Each thread thus reads every column's
+// packed offsets / weights once for two rows: the broadcast shared-memory loads of
+// those data, not the ex2 or the FMA pipe, bounded a one-row-per-thread epilogue.
+// Warp 8 issues TMA loads, warp 9 issues tcgen05.mma.  Two TMEM buffers (2 x 128
+// columns: two 64-column halves each) let the MMAs of tile i+1 overlap the epilogue of
+// tile i; a 4-stage shared-memory ring feeds the streamed operand.
 //
 // Every mbarrier wait is bounded: on timeout the kernel records LAMP_E_TIMEOUT in
 // the device status word, stops issuing work, waits (bounded) for its own copies
@@ -33,16 +36,19 @@ namespace lamp {
 
 namespace tc {
 
-constexpr int kTile = 128;       // rows per A tile = columns per B tile = MMA M = N
+constexpr int kTile = 128;       // rows of a fixed half tile = MMA M; padding unit of the bf16 copies
+constexpr int kFixed = 2 * kTile;  // rows of the fixed tile (two MMA halves)
+constexpr int kStream = 64;      // rows of a streamed tile = MMA N
 constexpr int kK = 64;           // K extent (points zero-padded to 64 coordinates)
 constexpr int kStages = 4;       // streamed-operand ring
-constexpr int kTileBytes = kTile * kK * 2;  // 16 KiB per bf16 tile
+constexpr int kTileBytes = kTile * kK * 2;      // 16 KiB per 128-row bf16 half tile
+constexpr int kStreamBytes = kStream * kK * 2;  // 8 KiB per streamed bf16 tile
 constexpr int kEpiWarps = 8;      // two warps per TMEM lane quadrant, each takes half the columns
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kProducerWarp = kEpiWarps;
 constexpr int kMmaWarp = kEpiWarps + 1;
 constexpr int kThreads = (kEpiWarps + 2) * 32;
-constexpr uint32_t kTmemCols = 256;         // two 128-column FP32 accumulators
+constexpr uint32_t kTmemCols = 256;         // two buffers x two 64-column FP32 accumulators
 constexpr uint32_t kWaitLimit = 1u << 24;   // bounded spin on every mbarrier
 constexpr int kTimeoutStatus = 6;           // LAMP_E_TIMEOUT
 
@@ -161,21 +167,23 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 }
 
 
-// 32 consecutive FP32 columns of this warp's 32 TMEM lanes, load and wait in ONE asm
-// statement: the destination registers of tcgen05.ld are written asynchronously until
-// tcgen05.wait::ld, and if the two were separate statements the compiler could copy
-// or spill those registers in between (it believes they are already final).
-__device__ __forceinline__ void tmem_ld32_wait(uint32_t taddr, uint32_t (&v)[32]) {
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes at two addresses (the two
+// accumulator halves), loads and wait in ONE asm statement: the destination registers
+// of tcgen05.ld are written asynchronously until tcgen05.wait::ld, and if they were
+// separate statements the compiler could copy or spill those registers in between
+// (it believes they are already final).
+__device__ __forceinline__ void tmem_ld16x2_wait(uint32_t ta, uint32_t tb, uint32_t (&v)[32]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%32];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%33];\n\t"
       "tcgen05.wait::ld.sync.aligned;"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
         "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
         "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
         "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-      : "r"(taddr)
+      : "r"(ta), "r"(tb)
       : "memory");
 }
 
@@ -215,43 +223,42 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor, kind::f16: D fp32, A and B bf16, both K-major, M = N = 128.
-__host__ __device__ constexpr uint32_t idesc_bf16_128x128() {
-  return (1u << 4)                      // D format: f32
-         | (1u << 7)                    // A format: bf16
-         | (1u << 10)                   // B format: bf16
-         | ((uint32_t)(kTile >> 3) << 17)  // N >> 3
-         | ((uint32_t)(kTile >> 4) << 24); // M >> 4
+// Instruction descriptor, kind::f16: D fp32, A and B bf16, both K-major, M = 128, N = 64.
+__host__ __device__ constexpr uint32_t idesc_bf16_128x64() {
+  return (1u << 4)                        // D format: f32
+         | (1u << 7)                      // A format: bf16
+         | (1u << 10)                     // B format: bf16
+         | ((uint32_t)(kStream >> 3) << 17)  // N >> 3
+         | ((uint32_t)(kTile >> 4) << 24);   // M >> 4
 }
 
 // ROWS = true: G1 (fixed x tile, streamed y tiles, per-row sums of both streams)
-// ROWS = false: G2 (fixed y tile, streamed x tiles, per-column sums of both streams
-// and of z X for <C, X>)
+// ROWS = false: G2 (fixed y tile, streamed x tiles, per-column sums of both streams)
 // WC: column sweep of an evaluation pass (also accumulates sum_i z_ij X_ij for <C, X^t>)
+// map_fixed: 128-row boxes of the fixed operand; map_stream: 64-row boxes of the streamed one
 template <bool ROWS, int WC>
 __global__ void __launch_bounds__(kThreads, 2)
-k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_y, const Work w,
-           int64_t n, int64_t m, int tiles_per_split, const Consts k) {
+k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant__ CUtensorMap map_stream,
+           const Work w, int64_t n, int64_t m, int tiles_per_split, const Consts k) {
   DevState* __restrict__ dev = w.dev;
   if (dev->done) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment for the swizzled tiles
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* sFixed = smem;
-  unsigned char* sStream = smem + kTileBytes;
-  Bars* B = reinterpret_cast<Bars*>(smem + kTileBytes * (1 + kStages));
-  // per streamed tile, double-buffered: for each pair of entries p, two float4
-  //   [2p] = {-offA_2p, -offA_2p+1, wgtA_2p, wgtA_2p+1}, [2p+1] = the same for stream B
-  // (G1: column offsets / weights w_j; G2: row offsets / weights q_i), copied by TMA
-  // from the packed-pair arrays the finalize kernels write
+  unsigned char* sFixed = smem;                         // two 16 KiB halves
+  unsigned char* sStream = smem + 2 * kTileBytes;       // kStages x 8 KiB
+  Bars* B = reinterpret_cast<Bars*>(sStream + kStreamBytes * kStages);
+  // per streamed tile, double-buffered: the packed-pair data of its 64 entries (32 pairs,
+  // two float4 each; G1: column offsets / weights, G2: row offsets / weights), copied by
+  // a bulk copy from the packed-pair arrays the finalize kernels write
   float4* sPair = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(B) + kBarBytes);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int cur = dev->cur;
-  const int64_t fixed0 = (int64_t)blockIdx.x * kTile;  // first row (G1) / column (G2) of the fixed tile
+  const int64_t fixed0 = (int64_t)blockIdx.x * kFixed;  // first row (G1) / column (G2) of the fixed tile
   const int64_t nstream = ROWS ? m : n;
-  const int64_t ntiles_all = (nstream + kTile - 1) / kTile;
+  const int64_t ntiles_all = (nstream + kStream - 1) / kStream;
   const int64_t it0 = (int64_t)blockIdx.y * tiles_per_split;
   int64_t it1 = it0 + tiles_per_split;
   if (it1 > ntiles_all) it1 = ntiles_all;
@@ -286,18 +293,21 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
     if (lane == 0) {
       const float4* __restrict__ pair_src = ROWS ? w.colq2[cur] : w.g2row2;
       int issued = 0, pissued = 0;
-      mbar_expect_tx(&B->fixed_full, kTileBytes);
-      tma_load_2d(sFixed, ROWS ? &map_x : &map_y, &B->fixed_full, 0, (int)fixed0);
+      // the fixed tile: two 128-row boxes (rows beyond the padded array read as zeros)
+      mbar_expect_tx(&B->fixed_full, 2 * kTileBytes);
+      tma_load_2d(sFixed, &map_fixed, &B->fixed_full, 0, (int)fixed0);
+      tma_load_2d(sFixed + kTileBytes, &map_fixed, &B->fixed_full, 0, (int)(fixed0 + kTile));
       for (int i = 0; i < ntiles; ++i) {
         const int s = i % kStages;
         const int b = i & 1;
         if (i >= kStages && !mbar_wait(&B->empty[s], ((i / kStages) & 1) ^ 1, B, dev)) break;
-        mbar_expect_tx(&B->full[s], kTileBytes);
-        tma_load_2d(sStream + s * kTileBytes, ROWS ? &map_y : &map_x, &B->full[s], 0, (int)((it0 + i) * kTile));
+        mbar_expect_tx(&B->full[s], kStreamBytes);
+        tma_load_2d(sStream + s * kStreamBytes, &map_stream, &B->full[s], 0, (int)((it0 + i) * kStream));
         issued = i + 1;
         if (i >= 2 && !mbar_wait(&B->pair_empty[b], ((i >> 1) - 1) & 1, B, dev)) break;
-        mbar_expect_tx(&B->pair_full[b], kTile * sizeof(float4));
-        bulk_load(sPair + (size_t)b * kTile, pair_src + (it0 + i) * kTile, kTile * sizeof(float4), &B->pair_full[b]);
+        mbar_expect_tx(&B->pair_full[b], kStream * sizeof(float4));
+        bulk_load(sPair + (size_t)b * kStream, pair_src + (it0 + i) * kStream, kStream * sizeof(float4),
+                  &B->pair_full[b]);
         pissued = i + 1;
       }
       if (*(volatile int*)&B->err) {
@@ -309,9 +319,9 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
       }
     }
   } else if (warp == kMmaWarp) {
-    // ---------------- MMA issuer: D[buffer] = A(fixed) * B(streamed)^T ----------------
+    // ------ MMA issuer: D[buffer][half a] = A(fixed half a) * B(streamed)^T, a = 0, 1 ------
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16_128x128();
+      const uint32_t idesc = idesc_bf16_128x64();
       int issued = 0;
       if (mbar_wait(&B->fixed_full, 0, B, dev)) {
         const uint32_t sF = smem_u32(sFixed);
@@ -322,10 +332,13 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
           if (!mbar_wait(&B->full[s], (i / kStages) & 1, B, dev)) break;
           if (i >= 2 && !mbar_wait(&B->tmem_empty[b], ((i >> 1) - 1) & 1, B, dev)) break;
           tc_fence_after();
-          const uint32_t bBase = sS + s * kTileBytes;
+          const uint32_t bBase = sS + s * kStreamBytes;
 #pragma unroll
-          for (int kk = 0; kk < kK / 16; ++kk)
-            umma_bf16(tmem + b * kTile, sdesc_sw128(sF + kk * 32), sdesc_sw128(bBase + kk * 32), idesc, kk > 0);
+          for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int kk = 0; kk < kK / 16; ++kk)
+              umma_bf16(tmem + b * (2 * kStream) + a * kStream, sdesc_sw128(sF + a * kTileBytes + kk * 32),
+                        sdesc_sw128(bBase + kk * 32), idesc, kk > 0);
           umma_commit(&B->empty[s]);
           umma_commit(&B->tmem_full[b]);
           issued = i + 1;
@@ -337,68 +350,38 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
       }
     }
   } else {
-    // ---------------- epilogue: warps 0-7; lane index t, column half h ----------------
-    const int t = (warp & 3) * 32 + lane;  // TMEM lane = row of D owned (0..127)
-    const int h = warp >> 2;               // which 64 of the 128 accumulator columns
+    // ------- epilogue: warps 0-7; TMEM lane t of both halves, 32-column slice h -------
+    const int t = (warp & 3) * 32 + lane;  // TMEM lane (0..127); rows t and 128 + t of the fixed tile
+    const int h = warp >> 2;               // columns [32 h, 32 h + 32) of each streamed tile
     const SweepParams sp = make_sweep_params(sweep_kappa(dev->kappa, k), k);
     const uint64_t ahA2 = pk(sp.ahA, sp.ahA), alA2 = pk(sp.alA, sp.alA);
     const float dal = (float)(sp.aB - sp.aA);  // stream B: v^B = (a^B - a^A) z + (v^A + dB)
     const uint64_t da2 = pk(dal, dal);
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;  // TMEM lane field
-    // this thread's own offsets (G1: its row's shift; G2: its column's offset, negated,
-    // and the column's dB as stored in the pair arrays)
-    uint64_t ownA2, ownD2 = 0ull;
-    const int64_t own = fixed0 + t;
-    if (ROWS) {
-      const float2 rq = w.rowshift[cur][own < n ? own : n - 1];
-      ownA2 = pk(-rq.x, -rq.x);
-    } else {
-      const float4 cq = w.colq[cur][own];  // padded columns: {+inf, 0, +inf, 0}
-      ownA2 = pk(-cq.x, -cq.x);
-      // the column's dB = BqA - BcolB, the same float the row sweep reads (padding: -2^100)
-      const float db = pair_dB(w.colq2[cur], own);
-      ownD2 = pk(db, db);
-    }
-    float hiA = 0.f, loA = 0.f, hiB = 0.f, loB = 0.f, hiC = 0.f, loC = 0.f;
-    // packed pair sums over this warp's 64 columns of a tile (two alternating accumulators)
-    uint64_t accA[2], accB[2], accC[2];
-    auto reset = [&]() {
-      accA[0] = accA[1] = accB[0] = accB[1] = accC[0] = accC[1] = 0ull;
-    };
-    auto fold = [&]() {
-      const float2 a2 = upk(f2add(accA[0], accA[1])), b2 = upk(f2add(accB[0], accB[1]));
-      ff_add(hiA, loA, a2.x + a2.y);
-      ff_add(hiB, loB, b2.x + b2.y);
-      if (WC) {
-        const float2 c2 = upk(f2add(accC[0], accC[1]));
-        ff_add(hiC, loC, c2.x + c2.y);
-      }
-    };
-    // 16 accumulator columns (8 pairs) starting at column col of the tile
-    auto half_chunk = [&](const uint32_t (&v)[16], const float4* pr, int col) {
+    // the own offsets of this thread's two fixed points (G1: the rows' shifts; G2: the
+    // columns' offsets, negated, and their dB as stored in the pair arrays); points past
+    // the end read a clamped (G1) or padding (G2) entry and are never written
+    uint64_t ownA2[2], ownD2[2] = {0ull, 0ull};
+    int64_t own[2];
 #pragma unroll
-      for (int p = 0; p < 8; ++p) {
-        const float4 qa = pr[col + 2 * p];
-        const float4 qb = pr[col + 2 * p + 1];
-        const uint64_t z2 = pk(__uint_as_float(v[2 * p]), __uint_as_float(v[2 * p + 1]));
-        const uint64_t vA = f2fma(alA2, z2, f2fma(ahA2, z2, f2add(ownA2, pk(qa.x, qa.y))));
-        // G1: the inner column's BqA - BqB from the pair data; G2: the own column's
-        const uint64_t vB = f2fma(da2, z2, f2add(vA, ROWS ? pk(qb.x, qb.y) : ownD2));
-        const float2 vAf = upk(vA), vBf = upk(vB);
-        const uint64_t eA = pk(ex2(vAf.x), ex2(vAf.y));
-        const uint64_t eB = pk(ex2(vBf.x), ex2(vBf.y));
-        if (WC) {
-          const uint64_t pA = f2mul(eA, pk(qa.z, qa.w));
-          accA[p & 1] = f2add(accA[p & 1], pA);
-          accC[p & 1] = f2fma(z2, pA, accC[p & 1]);
-        } else {
-          accA[p & 1] = f2fma(eA, pk(qa.z, qa.w), accA[p & 1]);
-        }
-        // G1: stream B's column weight is inside dB; G2: weight by the row's q^B
-        if (ROWS) accB[p & 1] = f2add(accB[p & 1], eB);
-        else accB[p & 1] = f2fma(eB, pk(qb.z, qb.w), accB[p & 1]);
+    for (int r = 0; r < 2; ++r) {
+      own[r] = fixed0 + r * kTile + t;
+      if (ROWS) {
+        const float2 rq = w.rowshift[cur][own[r] < n ? own[r] : n - 1];
+        ownA2[r] = pk(-rq.x, -rq.x);
+      } else {
+        const int64_t mp = (m + kTile - 1) / kTile * kTile;  // the column data are padded to mp
+        const int64_t oc = own[r] < mp ? own[r] : mp - 1;
+        const float4 cq = w.colq[cur][oc];  // padded columns: {+inf, 0, +inf, 0}
+        ownA2[r] = pk(-cq.x, -cq.x);
+        const float db = pair_dB(w.colq2[cur], oc);  // padding: -2^100
+        ownD2[r] = pk(db, db);
       }
-    };
+    }
+    float hiA[2] = {0.f, 0.f}, loA[2] = {0.f, 0.f}, hiB[2] = {0.f, 0.f}, loB[2] = {0.f, 0.f};
+    float hiC[2] = {0.f, 0.f}, loC[2] = {0.f, 0.f};
+    // packed pair sums of this thread's two points over one streamed tile
+    uint64_t accA[2], accB[2], accC[2];
     for (int i = 0; i < ntiles; ++i) {
       const int b = i & 1;
       bool ok = mbar_wait(&B->pair_full[b], (i >> 1) & 1, B, dev);
@@ -406,46 +389,86 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CU
       // warp-uniform decision before the .sync.aligned TMEM loads
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
-      const float4* pr = sPair + (size_t)b * kTile;
-      // this warp's 64 columns as two 32-column loads (each with its wait); other warps
-      // of the SM sub-partition cover the TMEM latency
-      const uint32_t tbase = tmem + lane_base + b * kTile + h * 64;
-      reset();
+      const float4* pr = sPair + (size_t)b * kStream;
+      const uint32_t tbase = tmem + lane_base + b * (2 * kStream) + h * 32;
+#pragma unroll
+      for (int r = 0; r < 2; ++r) accA[r] = accB[r] = accC[r] = 0ull;
 #pragma unroll 1
       for (int c = 0; c < 2; ++c) {
+        // 16 columns of both halves: v[0..15] row / column t, v[16..31] row / column 128 + t
         uint32_t v[32];
-        tmem_ld32_wait(tbase + c * 32, v);
-        half_chunk(*reinterpret_cast<const uint32_t(*)[16]>(&v[0]), pr, h * 64 + c * 32);
-        half_chunk(*reinterpret_cast<const uint32_t(*)[16]>(&v[16]), pr, h * 64 + c * 32 + 16);
+        tmem_ld16x2_wait(tbase + c * 16, tbase + kStream + c * 16, v);
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+          const int col = h * 32 + c * 16 + 2 * p;  // first column of the pair in the tile
+          const float4 qa = pr[col];
+          const float4 qb = pr[col + 1];
+          const uint64_t offA2 = pk(qa.x, qa.y), wA2 = pk(qa.z, qa.w);
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const uint64_t z2 = pk(__uint_as_float(v[16 * r + 2 * p]), __uint_as_float(v[16 * r + 2 * p + 1]));
+            const uint64_t vA = f2fma(alA2, z2, f2fma(ahA2, z2, f2add(ownA2[r], offA2)));
+            // G1: the inner column's dB from the pair data; G2: the own column's
+            const uint64_t vB = f2fma(da2, z2, f2add(vA, ROWS ? pk(qb.x, qb.y) : ownD2[r]));
+            const float2 vAf = upk(vA), vBf = upk(vB);
+            const uint64_t eA = pk(ex2(vAf.x), ex2(vAf.y));
+            const uint64_t eB = pk(ex2(vBf.x), ex2(vBf.y));
+            if (WC) {
+              const uint64_t pA = f2mul(eA, wA2);
+              accA[r] = f2add(accA[r], pA);
+              accC[r] = f2fma(z2, pA, accC[r]);
+            } else {
+              accA[r] = f2fma(eA, wA2, accA[r]);
+            }
+            // G1: stream B's column weight is inside dB; G2: weight by the row's q^B
+            if (ROWS) accB[r] = f2add(accB[r], eB);
+            else accB[r] = f2fma(eB, pk(qb.z, qb.w), accB[r]);
+          }
+        }
       }
-      fold();
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const float2 a2 = upk(accA[r]), b2 = upk(accB[r]);
+        ff_add(hiA[r], loA[r], a2.x + a2.y);
+        ff_add(hiB[r], loB[r], b2.x + b2.y);
+        if (WC) {
+          const float2 c2 = upk(accC[r]);
+          ff_add(hiC[r], loC[r], c2.x + c2.y);
+        }
+      }
       tc_fence_before();
       mbar_arrive(&B->tmem_empty[b]);
       mbar_arrive(&B->pair_empty[b]);
     }
-    // combine the two column halves of each lane (the stream ring is idle now: every
+    // combine the two column slices h of each point (the stream ring is idle now: every
     // loaded tile has been consumed by an MMA whose completion the epilogue waited for)
     double* comb = reinterpret_cast<double*>(sStream);
     if (h == 1) {
-      comb[t * 3 + 0] = (double)hiA + (double)loA;
-      comb[t * 3 + 1] = (double)hiB + (double)loB;
-      comb[t * 3 + 2] = (double)hiC + (double)loC;
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        comb[(r * kTile + t) * 3 + 0] = (double)hiA[r] + (double)loA[r];
+        comb[(r * kTile + t) * 3 + 1] = (double)hiB[r] + (double)loB[r];
+        comb[(r * kTile + t) * 3 + 2] = (double)hiC[r] + (double)loC[r];
+      }
     }
     epi_bar();
     if (h == 0 && !*(volatile int*)&B->err) {
-      const double sA = (double)hiA + (double)loA + comb[t * 3 + 0];
-      const double sB = (double)hiB + (double)loB + comb[t * 3 + 1];
-      const double sC = (double)hiC + (double)loC + comb[t * 3 + 2];
-      if (ROWS) {
-        if (own < n) {
-          w.rowpart[((int64_t)blockIdx.y * 2 + 0) * n + own] = sA;
-          w.rowpart[((int64_t)blockIdx.y * 2 + 1) * n + own] = sB;
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const double sA = (double)hiA[r] + (double)loA[r] + comb[(r * kTile + t) * 3 + 0];
+        const double sB = (double)hiB[r] + (double)loB[r] + comb[(r * kTile + t) * 3 + 1];
+        const double sC = (double)hiC[r] + (double)loC[r] + comb[(r * kTile + t) * 3 + 2];
+        if (ROWS) {
+          if (own[r] < n) {
+            w.rowpart[((int64_t)blockIdx.y * 2 + 0) * n + own[r]] = sA;
+            w.rowpart[((int64_t)blockIdx.y * 2 + 1) * n + own[r]] = sB;
+          }
+        } else if (own[r] < m) {
+          constexpr int na = WC ? 3 : 2;  // the layout k_col_fin reads for this pass
+          w.colpart[((int64_t)blockIdx.y * na + 0) * m + own[r]] = sA;
+          w.colpart[((int64_t)blockIdx.y * na + 1) * m + own[r]] = sB;
+          if (WC) w.colpart[((int64_t)blockIdx.y * na + 2) * m + own[r]] = sC;
         }
-      } else if (own < m) {
-        constexpr int na = WC ? 3 : 2;  // the layout k_col_fin reads for this pass
-        w.colpart[((int64_t)blockIdx.y * na + 0) * m + own] = sA;
-        w.colpart[((int64_t)blockIdx.y * na + 1) * m + own] = sB;
-        if (WC) w.colpart[((int64_t)blockIdx.y * na + 2) * m + own] = sC;
       }
     }
   }
@@ -520,8 +543,11 @@ int tc_wait_selftest(uint32_t polls, int* status) {
 }
 
 size_t tc_smem_bytes() {
-  // alignment slack + fixed tile + ring + barriers + packed pairs (2 x 128 float4)
-  return 1024 + (size_t)tc::kTileBytes * (1 + tc::kStages) + tc::kBarBytes + 2 * tc::kTile * sizeof(float4);
+  // alignment slack + fixed tile (two halves) + ring + barriers + packed pairs (2 x 64 float4);
+  // the ring also holds the epilogue's combine buffer (256 points x 3 doubles = 6 KiB)
+  static_assert(tc::kStreamBytes * tc::kStages >= tc::kFixed * 3 * 8, "combine buffer");
+  return 1024 + (size_t)tc::kTileBytes * 2 + (size_t)tc::kStreamBytes * tc::kStages + tc::kBarBytes +
+         2 * tc::kStream * sizeof(float4);
 }
 
 int64_t tc_pad(int64_t v) { return (v + tc::kTile - 1) / tc::kTile * tc::kTile; }
@@ -546,8 +572,9 @@ cudaError_t tc_fill_pairs(float4* a, int64_t count, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// encode a 2-D bf16 tensor map over a (rows_pad x 64) row-major array, 128 x 64 boxes, 128B swizzle
-cudaError_t tc_make_map(void* map_out, const void* base, int64_t rows_pad) {
+// encode a 2-D bf16 tensor map over a (rows_pad x 64) row-major array, box_rows x 64 boxes,
+// 128B swizzle (box_rows: 128 for the fixed halves, 64 for the streamed tiles)
+cudaError_t tc_make_map(void* map_out, const void* base, int64_t rows_pad, int box_rows) {
   typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -561,7 +588,7 @@ cudaError_t tc_make_map(void* map_out, const void* base, int64_t rows_pad) {
   }
   cuuint64_t dims[2] = {(cuuint64_t)tc::kK, (cuuint64_t)rows_pad};
   cuuint64_t strides[1] = {(cuuint64_t)tc::kK * 2};
-  cuuint32_t box[2] = {(cuuint32_t)tc::kK, (cuuint32_t)tc::kTile};
+  cuuint32_t box[2] = {(cuuint32_t)tc::kK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base),
                   dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -571,40 +598,55 @@ cudaError_t tc_make_map(void* map_out, const void* base, int64_t rows_pad) {
 
 cudaError_t tc_prepare() {
   const int sm = (int)tc_smem_bytes();
-  cudaError_t e = cudaFuncSetAttribute(tc::k_tc_sweep<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(tc::k_tc_sweep<false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(tc::k_tc_sweep<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaError_t e = cudaSuccess;
+  for (const void* f : {(const void*)tc::k_tc_sweep<true, 0>, (const void*)tc::k_tc_sweep<false, 0>,
+                        (const void*)tc::k_tc_sweep<false, 1>}) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    // prefer the largest shared-memory carveout: two CTAs per SM need 2 x ~69 KB
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  }
   return e;
 }
 
 int tc_blocks_per_sm(int which) {
-  int nb = 0;
-  if (which == 0)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tc::k_tc_sweep<true, 0>, tc::kThreads, tc_smem_bytes());
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tc::k_tc_sweep<false, 1>, tc::kThreads, tc_smem_bytes());
-  // two 256-column TMEM allocations fill the 512 columns of an SM
+  // resident CTAs per SM from the kernel's registers, its shared memory and TMEM (two
+  // 256-column allocations fill the 512 columns of an SM); the occupancy API assumes the
+  // default shared-memory carveout and undercounts, while the sweeps run at the maximum
+  cudaFuncAttributes fa{};
+  cudaError_t e = which == 0 ? cudaFuncGetAttributes(&fa, tc::k_tc_sweep<true, 0>)
+                             : cudaFuncGetAttributes(&fa, tc::k_tc_sweep<false, 1>);
+  int dev = 0, smem_sm = 0, regs_sm = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  if (e != cudaSuccess || fa.numRegs <= 0) return 1;
+  const int by_regs = regs_sm / (fa.numRegs * tc::kThreads);
+  const int by_smem = smem_sm / (int)(tc_smem_bytes() + fa.sharedSizeBytes + 1024);
+  int nb = by_regs < by_smem ? by_regs : by_smem;
   if (nb > 2) nb = 2;
   return nb > 0 ? nb : 1;
 }
 
-cudaError_t tc_launch_sweep(bool rows, int eval, const void* map_x, const void* map_y, const Work& w,
-                            const Consts& k, int splits, cudaStream_t st) {
+int tc_tile_fixed() { return tc::kFixed; }
+int tc_tile_stream() { return tc::kStream; }
+
+cudaError_t tc_launch_sweep(bool rows, int eval, const Geometry& g, const Work& w, const Consts& k, int splits,
+                            cudaStream_t st) {
   const int64_t nfixed = rows ? k.n : k.m;
   const int64_t nstream = rows ? k.m : k.n;
-  const int64_t ntiles = (nstream + tc::kTile - 1) / tc::kTile;
+  const int64_t ntiles = (nstream + tc::kStream - 1) / tc::kStream;
   const int tps = (int)((ntiles + splits - 1) / splits);
-  dim3 grid((unsigned)((nfixed + tc::kTile - 1) / tc::kTile), (unsigned)splits);
-  const CUtensorMap& mx = *reinterpret_cast<const CUtensorMap*>(map_x);
-  const CUtensorMap& my = *reinterpret_cast<const CUtensorMap*>(map_y);
+  dim3 grid((unsigned)((nfixed + tc::kFixed - 1) / tc::kFixed), (unsigned)splits);
+  // G1: x fixed (128-row boxes), y streamed (64-row boxes); G2: the reverse
+  const CUtensorMap& mf = *reinterpret_cast<const CUtensorMap*>(rows ? g.map_x : g.map_y);
+  const CUtensorMap& ms = *reinterpret_cast<const CUtensorMap*>(rows ? g.map_y64 : g.map_x64);
   if (rows)
-    tc::k_tc_sweep<true, 0><<<grid, tc::kThreads, tc_smem_bytes(), st>>>(mx, my, w, k.n, k.m, tps, k);
+    tc::k_tc_sweep<true, 0><<<grid, tc::kThreads, tc_smem_bytes(), st>>>(mf, ms, w, k.n, k.m, tps, k);
   else if (eval)
-    tc::k_tc_sweep<false, 1><<<grid, tc::kThreads, tc_smem_bytes(), st>>>(mx, my, w, k.n, k.m, tps, k);
+    tc::k_tc_sweep<false, 1><<<grid, tc::kThreads, tc_smem_bytes(), st>>>(mf, ms, w, k.n, k.m, tps, k);
   else
-    tc::k_tc_sweep<false, 0><<<grid, tc::kThreads, tc_smem_bytes(), st>>>(mx, my, w, k.n, k.m, tps, k);
+    tc::k_tc_sweep<false, 0><<<grid, tc::kThreads, tc_smem_bytes(), st>>>(mf, ms, w, k.n, k.m, tps, k);
   return cudaGetLastError();
 }
 
