@@ -310,10 +310,10 @@ def run_gpu(args, rank, world):
         k32 = s32.time_kernels(3)
         fp32 = {"value": n * m / (ms32 / 1e3), "ms_per_step": ms32, "kernel_ms": k32}
         if args.ttt:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()  # from context creation: the K pass and the prime pass count
             s32b = L.Lamp(r, c, x=x, y=y, cost_scale=w.cost_scale, max_iter=args.ttt_max_iter,
                           **dict(params, prec="fp32"))
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
             rr = s32b.solve()
             fp32["time_to_tol"] = {"seconds": time.perf_counter() - t0, "iters": rr["iters"],
                                    "infeas": rr["infeas"], "converged": rr["converged"], "tol": w.tol}
@@ -322,11 +322,12 @@ def run_gpu(args, rank, world):
         s32.close()
         info["fp32_path"] = fp32
     if rank == 0 and args.ttt:
-        # time to infeasibility <= tol from the Alg. 2 start, through lamp_solve
-        s2 = L.Lamp(r, c, x=x, y=y, cost_scale=w.cost_scale, max_iter=args.ttt_max_iter,
-                    **params) if w.kind != "dense" else L.Lamp(r, c, C=C, max_iter=args.ttt_max_iter, **params)
+        # time to infeasibility <= tol from the Alg. 2 start: context creation (K pass,
+        # row-shift prime pass) and lamp_solve
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        s2 = L.Lamp(r, c, x=x, y=y, cost_scale=w.cost_scale, max_iter=args.ttt_max_iter,
+                    **params) if w.kind != "dense" else L.Lamp(r, c, C=C, max_iter=args.ttt_max_iter, **params)
         res = s2.solve()
         el = time.perf_counter() - t0
         info["time_to_tol"] = {"seconds": el, "iters": res["iters"], "infeas": res["infeas"],
