@@ -334,6 +334,23 @@ def run_gpu(args, rank, world):
                                "converged": res["converged"], "tol": w.tol}
         info["cost_at_tol"] = s2.objective()["cost"]
         s2.close()
+        if w.kind != "dense":
+            # the autograd form: lamp_ot_loss forward (context creation, solve to tol, objective)
+            # and the hand-written backward (lamp_grad)
+            xg = x.clone().requires_grad_(True)
+            yg = y.clone().requires_grad_(True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            loss = L.lamp_ot_loss(xg, yg, r=r, c=c, eta=w.eta, cost_scale=w.cost_scale, prec=args.prec, tol=w.tol,
+                                  max_iter=args.ttt_max_iter, check_every=args.check_every)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            loss.backward()
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            info["autograd_form"] = {"forward_s": t1 - t0, "backward_s": t2 - t1, "total_s": t2 - t0,
+                                     "loss": float(loss.item()),
+                                     "grad_finite": bool(torch.isfinite(xg.grad).all() and torch.isfinite(yg.grad).all())}
 
     if rank != 0:
         if dist:

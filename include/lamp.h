@@ -208,7 +208,9 @@ LAMP_API int lamp_round(lamp_ctx* ctx, double out[4], double* y, double* delta_r
  * to the points (envelope theorem): dL/dx_i = sum_j X_ij dC_ij/dx_i and
  * dL/dy_j = sum_i X_ij dC_ij/dy_j, with dC_ij/dx_i = 2 s (x_i - y_j).
  * dx: device n x d float32, dy: device m x d float32 (either may be NULL).
- * SQEUCLID only (LAMP_E_UNSUPPORTED otherwise).  Asynchronous. */
+ * One evaluation pass, then ceil(d / 8) recompute sweeps per side (X never stored).
+ * With LAMP_PREC_BF16_TC the points are the bf16-rounded ones the context solves
+ * with.  SQEUCLID only (LAMP_E_UNSUPPORTED otherwise).  Asynchronous. */
 LAMP_API int lamp_grad(lamp_ctx* ctx, float* dx, float* dy);
 
 /* Copy the state to host memory (synchronises).  nu, theta: m doubles; logZ:

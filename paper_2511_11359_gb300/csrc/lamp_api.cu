@@ -772,8 +772,10 @@ extern "C" int lamp_objective(lamp_ctx* ctx, double out[8]) {
 extern "C" int lamp_grad(lamp_ctx* ctx, float* dx, float* dy) {
   if (!ctx) return fail(nullptr, LAMP_E_INVALID, "lamp_grad: null context");
   if (ctx->pub_kind != LAMP_COST_SQEUCLID) return fail(ctx, LAMP_E_UNSUPPORTED, "lamp_grad needs LAMP_COST_SQEUCLID");
-  if (ctx->k.d > 8) return fail(ctx, LAMP_E_UNSUPPORTED, "lamp_grad supports d <= 8 in this build");
-  int rc = evaluate(ctx);
+  // d > 8: the gradient is computed in chunks of 8 coordinates (partials of 8 values per point)
+  int rc = ensure_part_width(ctx, std::min<int>((int)ctx->k.d, 8));
+  if (rc) return rc;
+  rc = evaluate(ctx);
   if (rc) return rc;
   CK(launch_grad(ctx->in, ctx->k, ctx->w, ctx->g, ctx->prec, dx, dy, ctx->stream));
   return LAMP_OK;

@@ -59,12 +59,12 @@ struct SweepIO {
 };
 
 // M_GRAD accumulates sum_b 2^{v_ab} weight_b V_b[0:DG] with V = Vin (n_in x DG, row-major)
-// when given, else the inner points' own coordinates (the gradient, DG = d)
+// when given, else coordinates q0 .. q0 + DG - 1 of the inner points (the gradient)
 template <int MODE, int DG, bool DIFF>
 __global__ void __launch_bounds__(kThreads, 1)
 k_pts_sweep(const float* __restrict__ P_out, const float* __restrict__ P_in, int64_t n_out, int64_t n_in, int d,
             const SweepIO io, double* __restrict__ part, float* __restrict__ pmax, int tiles_per_split,
-            const DevState* __restrict__ dev, const Consts k, const float* __restrict__ Vin) {
+            const DevState* __restrict__ dev, const Consts k, const float* __restrict__ Vin, int q0) {
   if ((MODE == M_ROWSUM || MODE == M_COLSUM) && dev->done) return;
   const int cur = dev->cur;
   const float2* __restrict__ off2 = cur ? io.off2[1] : io.off2[0];
@@ -265,7 +265,7 @@ k_pts_sweep(const float* __restrict__ P_out, const float* __restrict__ P_in, int
           const float vA = __fmaf_rn(alA, zz, __fmaf_rn(ahA, zz, -(oA[a] + dat[b].x)));
           const float pA = ex2(vA) * dat[b].y;
           const int ib = (b < 4) ? (tx * 4 + b) : (64 + tx * 4 + b - 4);
-          const float* src = Vin ? sV : sIn;
+          const float* src = Vin ? sV : sIn + q0 * kPT;
 #pragma unroll
           for (int q = 0; q < DG; ++q) g[q] = __fmaf_rn(pA, src[q * kPT + ib], g[q]);
         }
@@ -839,34 +839,36 @@ k_col_fin(const Work w, int splits, const double* __restrict__ cvec, int rowbloc
   }
 }
 
-// gradient finalize: dx_i = 2 s (r_i x_i - q_i acc_i), dy_j = 2 s (A_j y_j - w_j acc_j)
-__global__ void k_grad_fin(const double* __restrict__ part, int splits, int64_t np, int d, const float* __restrict__ P,
-                           const double* __restrict__ mass, const float4* __restrict__ wsrc, int wcomp,
-                           double s, float* __restrict__ out) {
+// gradient finalize of coordinates q0 .. q0 + dg - 1 (partials hold dg values per point):
+// dx_i = 2 s (r_i x_i - q_i acc_i)
+__global__ void k_grad_fin(const double* __restrict__ part, int splits, int64_t np, int dg, int q0, int d,
+                           const float* __restrict__ P, const double* __restrict__ mass,
+                           const float4* __restrict__ wsrc, int wcomp, double s, float* __restrict__ out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= np) return;
   float4 wq = wsrc[i];
   double wgt = (double)(wcomp == 1 ? wq.y : wq.w);
   double ms = mass[i];
-  for (int q = 0; q < d; ++q) {
+  for (int q = 0; q < dg; ++q) {
     double acc = 0.0;
-    for (int sp = 0; sp < splits; ++sp) acc += part[((int64_t)sp * np + i) * d + q];
-    out[i * d + q] = (float)(2.0 * s * (ms * (double)P[i * d + q] - wgt * acc));
+    for (int sp = 0; sp < splits; ++sp) acc += part[((int64_t)sp * np + i) * dg + q];
+    out[i * d + q0 + q] = (float)(2.0 * s * (ms * (double)P[i * d + q0 + q] - wgt * acc));
   }
 }
 
-// column gradient finalize: dy_j = 2 s (A_j y_j - w_j acc_j), w_j from the current column data
-__global__ void k_grad_fin_cols(const Work w, int splits, int64_t np, int d, const float* __restrict__ P, double s,
-                                float* __restrict__ out) {
+// column gradient finalize of coordinates q0 .. q0 + dg - 1: dy_j = 2 s (A_j y_j - w_j acc_j),
+// w_j from the current column data
+__global__ void k_grad_fin_cols(const Work w, int splits, int64_t np, int dg, int q0, int d,
+                                const float* __restrict__ P, double s, float* __restrict__ out) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= np) return;
   float4 cq = w.colq[w.dev->cur][j];
   double wgt = (double)cq.y;
   double ms = w.colA[j];
-  for (int q = 0; q < d; ++q) {
+  for (int q = 0; q < dg; ++q) {
     double acc = 0.0;
-    for (int sp = 0; sp < splits; ++sp) acc += w.colpart[((int64_t)sp * np + j) * d + q];
-    out[j * d + q] = (float)(2.0 * s * (ms * (double)P[j * d + q] - wgt * acc));
+    for (int sp = 0; sp < splits; ++sp) acc += w.colpart[((int64_t)sp * np + j) * dg + q];
+    out[j * d + q0 + q] = (float)(2.0 * s * (ms * (double)P[j * d + q0 + q] - wgt * acc));
   }
 }
 
@@ -890,13 +892,13 @@ static SweepIO io_same(const float2* o2, const float4* o4, const float4* in) {
 template <int MODE, int DG>
 static cudaError_t launch_pts(const float* Pout, const float* Pin, int64_t nout, int64_t nin, int d, const SweepIO& io,
                               double* part, float* pmax, int splits, const DevState* dev, const Consts& k,
-                              cudaStream_t st, const float* V = nullptr) {
+                              cudaStream_t st, const float* V = nullptr, int q0 = 0) {
   auto kern = k.zdot ? k_pts_sweep<MODE, DG, false> : k_pts_sweep<MODE, DG, true>;
   size_t sm = pts_smem(d, V ? DG : 0);
   int64_t tin = cdiv(nin, kPT);
   int tps = (int)cdiv(tin, splits);
   dim3 grid((unsigned)cdiv(nout, kPT), (unsigned)splits);
-  kern<<<grid, kThreads, sm, st>>>(Pout, Pin, nout, nin, d, io, part, pmax, tps, dev, k, V);
+  kern<<<grid, kThreads, sm, st>>>(Pout, Pin, nout, nin, d, io, part, pmax, tps, dev, k, V, q0);
   return cudaGetLastError();
 }
 
@@ -1085,18 +1087,19 @@ int tile_inner_cols(const Consts& k, int prec) {
   return k.kind == COST_DENSE ? kDColRows : uses_direct_sweeps(k, prec) ? kDirectTile : kPT;
 }
 
+// gradient coordinates q0 .. q0 + DG - 1 (one recompute sweep per side)
 template <int DG>
 static cudaError_t launch_grad_d(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, float* dx,
-                                 float* dy, cudaStream_t st) {
+                                 float* dy, int q0, cudaStream_t st) {
   if (dx) {
     // outer = rows (x), inner = columns (y): weights w_j of colq, outer offsets RqA of g2row
     SweepIO io;
     for (int b = 0; b < 2; ++b) { io.off2[b] = nullptr; io.off4[b] = w.g2row; io.indat[b] = w.colq[b]; }
     cudaError_t e = launch_pts<M_GRAD, DG>(in.x, in.y, k.n, k.m, k.d, io, w.rowpart, nullptr, g.rows_split, w.dev,
-                                           k, st);
+                                           k, st, nullptr, q0);
     if (e != cudaSuccess) return e;
-    k_grad_fin<<<(unsigned)cdiv(k.n, 256), 256, 0, st>>>(w.rowpart, g.rows_split, k.n, k.d, in.x, in.r, w.g2row, 1,
-                                                        k.s, dx);
+    k_grad_fin<<<(unsigned)cdiv(k.n, 256), 256, 0, st>>>(w.rowpart, g.rows_split, k.n, DG, q0, k.d, in.x, in.r,
+                                                        w.g2row, 1, k.s, dx);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1105,28 +1108,35 @@ static cudaError_t launch_grad_d(const Inputs& in, const Consts& k, const Work& 
     SweepIO io;
     for (int b = 0; b < 2; ++b) { io.off2[b] = nullptr; io.off4[b] = w.colq[b]; io.indat[b] = w.g2row; }
     cudaError_t e = launch_pts<M_GRAD, DG>(in.y, in.x, k.m, k.n, k.d, io, w.colpart, nullptr, g.cols_split, w.dev,
-                                           k, st);
+                                           k, st, nullptr, q0);
     if (e != cudaSuccess) return e;
-    k_grad_fin_cols<<<(unsigned)cdiv(k.m, 256), 256, 0, st>>>(w, g.cols_split, k.m, k.d, in.y, k.s, dy);
+    k_grad_fin_cols<<<(unsigned)cdiv(k.m, 256), 256, 0, st>>>(w, g.cols_split, k.m, DG, q0, k.d, in.y, k.s, dy);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
+// the gradient in chunks of up to 8 coordinates (the partial-sum buffers hold 8 values per
+// point when d > 8): ceil(d / 8) recompute sweeps per side
 cudaError_t launch_grad(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec, float* dx,
                         float* dy, cudaStream_t st) {
-  switch (k.d) {
-    case 1: return launch_grad_d<1>(in, k, w, g, dx, dy, st);
-    case 2: return launch_grad_d<2>(in, k, w, g, dx, dy, st);
-    case 3: return launch_grad_d<3>(in, k, w, g, dx, dy, st);
-    case 4: return launch_grad_d<4>(in, k, w, g, dx, dy, st);
-    case 5: return launch_grad_d<5>(in, k, w, g, dx, dy, st);
-    case 6: return launch_grad_d<6>(in, k, w, g, dx, dy, st);
-    case 7: return launch_grad_d<7>(in, k, w, g, dx, dy, st);
-    case 8: return launch_grad_d<8>(in, k, w, g, dx, dy, st);
-    default: return cudaErrorNotSupported;
+  for (int q0 = 0; q0 < k.d; q0 += 8) {
+    const int dg = k.d - q0 < 8 ? k.d - q0 : 8;
+    cudaError_t e;
+    switch (dg) {
+      case 1: e = launch_grad_d<1>(in, k, w, g, dx, dy, q0, st); break;
+      case 2: e = launch_grad_d<2>(in, k, w, g, dx, dy, q0, st); break;
+      case 3: e = launch_grad_d<3>(in, k, w, g, dx, dy, q0, st); break;
+      case 4: e = launch_grad_d<4>(in, k, w, g, dx, dy, q0, st); break;
+      case 5: e = launch_grad_d<5>(in, k, w, g, dx, dy, q0, st); break;
+      case 6: e = launch_grad_d<6>(in, k, w, g, dx, dy, q0, st); break;
+      case 7: e = launch_grad_d<7>(in, k, w, g, dx, dy, q0, st); break;
+      default: e = launch_grad_d<8>(in, k, w, g, dx, dy, q0, st); break;
+    }
+    if (e != cudaSuccess) return e;
   }
+  return cudaSuccess;
 }
 
 // ------------------------------------------------------------------------------------------
