@@ -39,6 +39,33 @@ __device__ __forceinline__ float warp_min_f(float v) {
 
 // ------------------------------------------------------------------------------------------
 // sweeps over point clouds (LAMP_COST_SQEUCLID, float32 CUDA-core x.y)
+
+// stage a tile of 128 points (rows base.., np valid) x d coordinates into s[kk * 128 + p]:
+// thread (p = idx % 128, coordinate quad) reads up to 4 consecutive coordinates of one
+// point (one 16-byte load when d % 4 == 0) and consecutive threads write consecutive p,
+// so the transposed shared stores are free of bank conflicts
+__device__ __forceinline__ void stage_points(float* __restrict__ s, const float* __restrict__ P, int64_t base,
+                                             int64_t np, int d, int tid, int nthreads) {
+  const int dq = (d + 3) >> 2;
+  for (int idx = tid; idx < 128 * dq; idx += nthreads) {
+    const int p = idx & 127, kq = (idx >> 7) << 2;
+    const int64_t g = base + p;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (g < np) {
+      if ((d & 3) == 0) {
+        const float4 t = *reinterpret_cast<const float4*>(P + g * d + kq);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (kq + q < d) v[q] = P[g * d + kq + q];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (kq + q < d) s[(kq + q) * 128 + p] = v[q];
+  }
+}
 //
 // A CTA of 256 threads owns 128 "outer" points and loops over tiles of 128
 // "inner" points; each thread computes an 8x8 block of z = x.y (outer rows
@@ -61,7 +88,7 @@ struct SweepIO {
 // M_GRAD accumulates sum_b 2^{v_ab} weight_b V_b[0:DG] with V = Vin (n_in x DG, row-major)
 // when given, else coordinates q0 .. q0 + DG - 1 of the inner points (the gradient)
 template <int MODE, int DG, bool DIFF>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, MODE == M_GRAD ? 1 : 2)
 k_pts_sweep(const float* __restrict__ P_out, const float* __restrict__ P_in, int64_t n_out, int64_t n_in, int d,
             const SweepIO io, double* __restrict__ part, float* __restrict__ pmax, int tiles_per_split,
             const DevState* __restrict__ dev, const Consts k, const float* __restrict__ Vin, int q0) {
@@ -88,11 +115,7 @@ k_pts_sweep(const float* __restrict__ P_out, const float* __restrict__ P_in, int
 
   SweepParams sp = make_sweep_params(sweep_kappa(dev->kappa, k), k);
 
-  for (int idx = tid; idx < d * kPT; idx += kThreads) {
-    int p = idx / d, kk = idx - p * d;
-    int64_t go = o0 + p;
-    sOut[kk * kPT + p] = go < n_out ? P_out[go * d + kk] : 0.0f;
-  }
+  stage_points(sOut, P_out, o0, n_out, d, tid, kThreads);
 
   // outer offsets of this thread's 8 outer points
   float oA[8], oB[8];
@@ -137,11 +160,7 @@ k_pts_sweep(const float* __restrict__ P_out, const float* __restrict__ P_in, int
   for (int64_t it = it0; it < it1; ++it) {
     const int64_t i0 = it * kPT;
     __syncthreads();
-    for (int idx = tid; idx < d * kPT; idx += kThreads) {
-      int p = idx / d, kk = idx - p * d;
-      int64_t gi = i0 + p;
-      sIn[kk * kPT + p] = gi < n_in ? P_in[gi * d + kk] : 0.0f;
-    }
+    stage_points(sIn, P_in, i0, n_in, d, tid, kThreads);
     if (MODE == M_GRAD && Vin) {
       for (int idx = tid; idx < DG * kPT; idx += kThreads) {
         int p = idx / (DG > 0 ? DG : 1), q = idx - p * (DG > 0 ? DG : 1);
