@@ -353,7 +353,8 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
   // the transport map widens the buffers on first use (ensure_part_width)
   const size_t gradd = k.kind == COST_SQEUCLID ? (size_t)std::min<int64_t>(std::max<int64_t>(k.d, 2), 8) : 2;
   ctx->part_width = (int)std::max<size_t>(3, gradd);
-  // column / row data are padded to 128-entry multiples (padding entries contribute nothing)
+  // column / row data are padded to whole tiles of every sweep (tc_pad: a multiple of 128;
+  // padding entries contribute nothing)
   const size_t m_pad = (size_t)tc_pad(k.m), n_pad = (size_t)tc_pad(k.n);
   for (int b = 0; b < 2; ++b) {
     if ((rc = dalloc(ctx, &w.nu[b], m))) return bail(rc);

@@ -43,8 +43,15 @@ constexpr int kK = 64;           // K extent (points zero-padded to 64 coordinat
 constexpr int kStages = 4;       // streamed-operand ring
 constexpr int kTileBytes = kTile * kK * 2;      // 16 KiB per 128-row bf16 half tile
 constexpr int kStreamBytes = kStream * kK * 2;  // 8 KiB per streamed bf16 tile
-constexpr int kEpiWarps = 8;      // two warps per TMEM lane quadrant, each takes half the columns
+constexpr int kEpiWarps = 8;      // kSlices warps per TMEM lane quadrant, one column slice each
 constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kSlices = kEpiWarps / 4;            // column slices of a streamed tile
+constexpr int kSliceCols = kStream / kSlices;     // columns per slice (multiple of 16)
+static_assert(kEpiWarps % 4 == 0 && kStream % kSlices == 0 && kSliceCols % 16 == 0, "epilogue layout");
+// padding unit of the bf16 copies and of the per-point data arrays: whole fixed halves and
+// whole streamed tiles, lcm(kTile, kStream)
+constexpr int64_t gcd_c(int64_t a, int64_t b) { return b == 0 ? a : gcd_c(b, a % b); }
+constexpr int64_t kPad = kTile / gcd_c(kTile, kStream) * kStream;
 constexpr int kProducerWarp = kEpiWarps;
 constexpr int kMmaWarp = kEpiWarps + 1;
 constexpr int kThreads = (kEpiWarps + 2) * 32;
@@ -350,9 +357,9 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
       }
     }
   } else {
-    // ------- epilogue: warps 0-7; TMEM lane t of both halves, 32-column slice h -------
+    // ---- epilogue: warps 0 .. kEpiWarps-1; TMEM lane t of both halves, column slice h ----
     const int t = (warp & 3) * 32 + lane;  // TMEM lane (0..127); rows t and 128 + t of the fixed tile
-    const int h = warp >> 2;               // columns [32 h, 32 h + 32) of each streamed tile
+    const int h = warp >> 2;               // columns [h kSliceCols, (h + 1) kSliceCols) of each streamed tile
     const SweepParams sp = make_sweep_params(sweep_kappa(dev->kappa, k), k);
     const uint64_t ahA2 = pk(sp.ahA, sp.ahA), alA2 = pk(sp.alA, sp.alA);
     const float dal = (float)(sp.aB - sp.aA);  // stream B: v^B = (a^B - a^A) z + (v^A + dB)
@@ -370,7 +377,7 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
         const float2 rq = w.rowshift[cur][own[r] < n ? own[r] : n - 1];
         ownA2[r] = pk(-rq.x, -rq.x);
       } else {
-        const int64_t mp = (m + kTile - 1) / kTile * kTile;  // the column data are padded to mp
+        const int64_t mp = (m + kPad - 1) / kPad * kPad;  // the column data are padded to mp
         const int64_t oc = own[r] < mp ? own[r] : mp - 1;
         const float4 cq = w.colq[cur][oc];  // padded columns: {+inf, 0, +inf, 0}
         ownA2[r] = pk(-cq.x, -cq.x);
@@ -390,17 +397,17 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
       const float4* pr = sPair + (size_t)b * kStream;
-      const uint32_t tbase = tmem + lane_base + b * (2 * kStream) + h * 32;
+      const uint32_t tbase = tmem + lane_base + b * (2 * kStream) + h * kSliceCols;
 #pragma unroll
       for (int r = 0; r < 2; ++r) accA[r] = accB[r] = accC[r] = 0ull;
-#pragma unroll 1
-      for (int c = 0; c < 2; ++c) {
+#pragma unroll
+      for (int c = 0; c < kSliceCols / 16; ++c) {
         // 16 columns of both halves: v[0..15] row / column t, v[16..31] row / column 128 + t
         uint32_t v[32];
         tmem_ld16x2_wait(tbase + c * 16, tbase + kStream + c * 16, v);
 #pragma unroll
         for (int p = 0; p < 8; ++p) {
-          const int col = h * 32 + c * 16 + 2 * p;  // first column of the pair in the tile
+          const int col = h * kSliceCols + c * 16 + 2 * p;  // first column of the pair in the tile
           const float4 qa = pr[col];
           const float4 qb = pr[col + 1];
           const uint64_t offA2 = pk(qa.x, qa.y), wA2 = pk(qa.z, qa.w);
@@ -440,24 +447,31 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
       mbar_arrive(&B->tmem_empty[b]);
       mbar_arrive(&B->pair_empty[b]);
     }
-    // combine the two column slices h of each point (the stream ring is idle now: every
-    // loaded tile has been consumed by an MMA whose completion the epilogue waited for)
+    // combine the column slices h of each point (the stream ring is idle now: every loaded
+    // tile has been consumed by an MMA whose completion the epilogue waited for)
     double* comb = reinterpret_cast<double*>(sStream);
-    if (h == 1) {
+    if (h >= 1) {
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
-        comb[(r * kTile + t) * 3 + 0] = (double)hiA[r] + (double)loA[r];
-        comb[(r * kTile + t) * 3 + 1] = (double)hiB[r] + (double)loB[r];
-        comb[(r * kTile + t) * 3 + 2] = (double)hiC[r] + (double)loC[r];
+        double* cb = comb + ((size_t)(h - 1) * kFixed + r * kTile + t) * 3;
+        cb[0] = (double)hiA[r] + (double)loA[r];
+        cb[1] = (double)hiB[r] + (double)loB[r];
+        cb[2] = (double)hiC[r] + (double)loC[r];
       }
     }
     epi_bar();
     if (h == 0 && !*(volatile int*)&B->err) {
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
-        const double sA = (double)hiA[r] + (double)loA[r] + comb[(r * kTile + t) * 3 + 0];
-        const double sB = (double)hiB[r] + (double)loB[r] + comb[(r * kTile + t) * 3 + 1];
-        const double sC = (double)hiC[r] + (double)loC[r] + comb[(r * kTile + t) * 3 + 2];
+        double sA = (double)hiA[r] + (double)loA[r];
+        double sB = (double)hiB[r] + (double)loB[r];
+        double sC = (double)hiC[r] + (double)loC[r];
+        for (int hh = 1; hh < kSlices; ++hh) {
+          const double* cb = comb + ((size_t)(hh - 1) * kFixed + r * kTile + t) * 3;
+          sA += cb[0];
+          sB += cb[1];
+          sC += cb[2];
+        }
         if (ROWS) {
           if (own[r] < n) {
             w.rowpart[((int64_t)blockIdx.y * 2 + 0) * n + own[r]] = sA;
@@ -545,12 +559,12 @@ int tc_wait_selftest(uint32_t polls, int* status) {
 size_t tc_smem_bytes() {
   // alignment slack + fixed tile (two halves) + ring + barriers + packed pairs (2 x 64 float4);
   // the ring also holds the epilogue's combine buffer (256 points x 3 doubles = 6 KiB)
-  static_assert(tc::kStreamBytes * tc::kStages >= tc::kFixed * 3 * 8, "combine buffer");
+  static_assert(tc::kStreamBytes * tc::kStages >= (tc::kSlices - 1) * tc::kFixed * 3 * 8, "combine buffer");
   return 1024 + (size_t)tc::kTileBytes * 2 + (size_t)tc::kStreamBytes * tc::kStages + tc::kBarBytes +
          2 * tc::kStream * sizeof(float4);
 }
 
-int64_t tc_pad(int64_t v) { return (v + tc::kTile - 1) / tc::kTile * tc::kTile; }
+int64_t tc_pad(int64_t v) { return (v + tc::kPad - 1) / tc::kPad * tc::kPad; }
 
 cudaError_t tc_convert(const float* P, int64_t np, int d, float* Pr, void* Pb, cudaStream_t st) {
   const int64_t np_pad = tc_pad(np);
