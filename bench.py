@@ -98,6 +98,7 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.first = 0
 
     def start(self):
         try:
@@ -108,6 +109,15 @@ class ClockSampler:
             self.thread.start()
         except FileNotFoundError:
             self.proc = None
+            return
+        # wait (at most 3 s) until nvidia-smi reports, so the timed region is sampled from its
+        # start; samples taken before mark() are dropped
+        t0 = time.perf_counter()
+        while not self.lines and time.perf_counter() - t0 < 3.0:
+            time.sleep(0.02)
+
+    def mark(self):
+        self.first = len(self.lines)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -123,7 +133,7 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[self.first:]:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -248,8 +258,11 @@ def run_gpu(args, rank, world):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    # clocks are sampled over every GPU-timed measurement of the line: the timed steps, the
+    # per-kernel timing, the end-to-end steps, the float32 comparison and the solves to tolerance
     sampler = ClockSampler(local)
     sampler.start()
+    sampler.mark()
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     for i in range(args.steps):
@@ -263,7 +276,6 @@ def run_gpu(args, rank, world):
     total_ms = sum(a.elapsed_time(b) for a, b in evs)
     # per-kernel device times, measured with events between the launches
     kern_ms = solver.time_kernels(max(3, min(args.steps, 10)))
-    clocks = sampler.stop()
     value, total_s = job_throughput(n * m * args.steps, total_ms / 1e3, dist, devc)
     total_ms = total_s * 1e3
 
@@ -352,6 +364,7 @@ def run_gpu(args, rank, world):
                                      "loss": float(loss.item()),
                                      "grad_finite": bool(torch.isfinite(xg.grad).all() and torch.isfinite(yg.grad).all())}
 
+    clocks = sampler.stop()
     if rank != 0:
         if dist:
             dist.destroy_process_group()

@@ -155,6 +155,12 @@ __device__ __forceinline__ void tc_fence_before() {
 
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// orders this thread's generic-proxy accesses of shared memory before later async-proxy
+// accesses (bulk copies) that other threads issue after synchronising with it
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (bf16 in, fp32 accumulate)
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t accumulate) {
@@ -445,11 +451,14 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
       }
       tc_fence_before();
       mbar_arrive(&B->tmem_empty[b]);
+      // the pair buffer was read through the generic proxy and the producer's next bulk
+      // copy into it is an async-proxy write: without the proxy fence that write can
+      // overtake these reads (a write-after-read race across proxies)
+      fence_proxy_async_smem();
       mbar_arrive(&B->pair_empty[b]);
     }
-    // combine the column slices h of each point (the stream ring is idle now: every loaded
-    // tile has been consumed by an MMA whose completion the epilogue waited for)
-    double* comb = reinterpret_cast<double*>(sStream);
+    // combine the column slices h of each point in a buffer of its own (generic proxy only)
+    double* comb = reinterpret_cast<double*>(sPair + 2 * kStream);
     if (h >= 1) {
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
@@ -557,11 +566,10 @@ int tc_wait_selftest(uint32_t polls, int* status) {
 }
 
 size_t tc_smem_bytes() {
-  // alignment slack + fixed tile (two halves) + ring + barriers + packed pairs (2 x 64 float4);
-  // the ring also holds the epilogue's combine buffer (256 points x 3 doubles = 6 KiB)
-  static_assert(tc::kStreamBytes * tc::kStages >= (tc::kSlices - 1) * tc::kFixed * 3 * 8, "combine buffer");
+  // alignment slack + fixed tile (two halves) + ring + barriers + packed pairs (2 x 64 float4)
+  // + the epilogue's combine buffer ((slices - 1) x 256 points x 3 doubles)
   return 1024 + (size_t)tc::kTileBytes * 2 + (size_t)tc::kStreamBytes * tc::kStages + tc::kBarBytes +
-         2 * tc::kStream * sizeof(float4);
+         2 * tc::kStream * sizeof(float4) + (size_t)(tc::kSlices - 1) * tc::kFixed * 3 * sizeof(double);
 }
 
 int64_t tc_pad(int64_t v) { return (v + tc::kPad - 1) / tc::kPad * tc::kPad; }
@@ -616,7 +624,7 @@ cudaError_t tc_prepare() {
   for (const void* f : {(const void*)tc::k_tc_sweep<true, 0>, (const void*)tc::k_tc_sweep<false, 0>,
                         (const void*)tc::k_tc_sweep<false, 1>}) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    // prefer the largest shared-memory carveout: two CTAs per SM need 2 x ~69 KB
+    // prefer the largest shared-memory carveout: two CTAs per SM need 2 x ~75 KB
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   }

@@ -7,7 +7,8 @@ import pytest
 
 import oracle as O
 import workloads as W
-from tests.gpu_util import POT_TOL, RES_FLOOR, assert_logZ_close, assert_pot_close, gpu_solver, oracle_cost
+from tests.gpu_util import (POT_TOL, RES_FLOOR, assert_logZ_close, assert_pot_close, gpu_solver, gpu_solver_raw,
+                            oracle_cost)
 
 pytestmark = pytest.mark.gpu
 
@@ -138,14 +139,19 @@ def test_tc_solve_4096_converges_like_fp32():
     assert abs(its["bf16_tc"] - its["fp32"]) <= 0.1 * its["fp32"], its
 
 
-def test_tc_run_is_deterministic_across_graph_lengths():
+@pytest.mark.parametrize("n,iters", [(8192, 400), (1 << 15, 600)])
+def test_tc_run_is_deterministic_across_graph_lengths(n, iters):
     """The same bf16 problem iterated with different device-loop lengths gives bit-identical
-    potentials (no race in the pipelined kernels; many tiles per CTA at n = 8192)."""
-    w = W.highdim(n=8192, seed=21)
+    potentials and row shifts (no race in the pipelined kernels).  n = 2^15, d = 64 is the
+    full-size highdim workload: 74 streamed tiles per CTA, three waves of CTAs; a
+    write-after-read race between the epilogue's reads of a packed-pair buffer and the
+    next bulk copy into it once changed ~10 % of its iterations."""
+    w = W.highdim(n=n, seed=21)
     out = []
     for ce in (50, 7):
-        s, C, K = gpu_solver(w, prec="bf16_tc", check_every=ce)
-        s.iterate(400)
+        s = gpu_solver_raw(w, None, prec="bf16_tc", check_every=ce)  # K from the device pass
+        s.iterate(iters)
         out.append(s.get_state())
         s.close()
-    assert np.array_equal(out[0]["nu"], out[1]["nu"]) and np.array_equal(out[0]["theta"], out[1]["theta"])
+    for key in ("nu", "theta", "row_shifts"):
+        assert np.array_equal(out[0][key], out[1][key]), key
