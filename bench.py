@@ -351,6 +351,10 @@ def run_gpu(args, rank, world):
             # and the hand-written backward (lamp_grad)
             xg = x.clone().requires_grad_(True)
             yg = y.clone().requires_grad_(True)
+            # PyTorch starts its autograd device threads on the first backward of a process
+            # (0.1 - 1.5 s on the Arm hosts): a tiny unrelated backward takes that cost
+            warm = torch.ones(2, device=devc, requires_grad=True)
+            (warm * 2.0).sum().backward()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             loss = L.lamp_ot_loss(xg, yg, r=r, c=c, eta=w.eta, cost_scale=w.cost_scale, prec=args.prec, tol=w.tol,

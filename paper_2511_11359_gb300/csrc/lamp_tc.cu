@@ -47,7 +47,7 @@ constexpr int kEpiWarps = 8;      // kSlices warps per TMEM lane quadrant, one c
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kSlices = kEpiWarps / 4;            // column slices of a streamed tile
 constexpr int kSliceCols = kStream / kSlices;     // columns per slice (multiple of 16)
-static_assert(kEpiWarps % 4 == 0 && kStream % kSlices == 0 && kSliceCols % 16 == 0, "epilogue layout");
+static_assert(kEpiWarps % 4 == 0 && kStream % kSlices == 0 && kSliceCols % 8 == 0, "epilogue layout");
 // padding unit of the bf16 copies and of the per-point data arrays: whole fixed halves and
 // whole streamed tiles, lcm(kTile, kStream)
 constexpr int64_t gcd_c(int64_t a, int64_t b) { return b == 0 ? a : gcd_c(b, a % b); }
@@ -180,24 +180,28 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 }
 
 
-// 16 consecutive FP32 columns of this warp's 32 TMEM lanes at two addresses (the two
-// accumulator halves), loads and wait in ONE asm statement: the destination registers
-// of tcgen05.ld are written asynchronously until tcgen05.wait::ld, and if they were
-// separate statements the compiler could copy or spill those registers in between
-// (it believes they are already final).
-__device__ __forceinline__ void tmem_ld16x2_wait(uint32_t ta, uint32_t tb, uint32_t (&v)[32]) {
+// 8 consecutive FP32 columns of this warp's 32 TMEM lanes at two addresses (the two
+// accumulator halves), without waiting: tcgen05.ld writes its destination registers
+// asynchronously, until tcgen05.wait::ld.
+__device__ __forceinline__ void tmem_ld8x2(uint32_t ta, uint32_t tb, uint32_t (&v)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%32];\n\t"
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%33];\n\t"
-      "tcgen05.wait::ld.sync.aligned;"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%16];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%17];"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
-        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
       : "r"(ta), "r"(tb)
       : "memory");
+}
+
+// wait for this thread's TMEM loads; the registers they write are in-out operands, so
+// the compiler orders every use (and any copy) of them after the wait
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+                 "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]),
+                 "+r"(v[15])
+               :
+               : "memory");
 }
 
 
@@ -367,7 +371,10 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
     const int t = (warp & 3) * 32 + lane;  // TMEM lane (0..127); rows t and 128 + t of the fixed tile
     const int h = warp >> 2;               // columns [h kSliceCols, (h + 1) kSliceCols) of each streamed tile
     const SweepParams sp = make_sweep_params(sweep_kappa(dev->kappa, k), k);
-    const uint64_t ahA2 = pk(sp.ahA, sp.ahA), alA2 = pk(sp.alA, sp.alA);
+    // v^A = a^A z + own + off with a^A rounded to float32 (ah): dropping the low part al
+    // changes v by at most half an ulp of a^A z, the order of the rounding of z itself in
+    // the MMA's FP32 accumulation (the float32 CUDA-core paths keep al)
+    const uint64_t ahA2 = pk(sp.ahA, sp.ahA);
     const float dal = (float)(sp.aB - sp.aA);  // stream B: v^B = (a^B - a^A) z + (v^A + dB)
     const uint64_t da2 = pk(dal, dal);
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;  // TMEM lane field
@@ -395,6 +402,8 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
     float hiC[2] = {0.f, 0.f}, loC[2] = {0.f, 0.f};
     // packed pair sums of this thread's two points over one streamed tile
     uint64_t accA[2], accB[2], accC[2];
+    uint32_t vv[2][16];  // two TMEM chunks: the one evaluated and the one in flight
+    constexpr int kChunks = kSliceCols / 8;
     for (int i = 0; i < ntiles; ++i) {
       const int b = i & 1;
       bool ok = mbar_wait(&B->pair_full[b], (i >> 1) & 1, B, dev);
@@ -406,21 +415,25 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
       const uint32_t tbase = tmem + lane_base + b * (2 * kStream) + h * kSliceCols;
 #pragma unroll
       for (int r = 0; r < 2; ++r) accA[r] = accB[r] = accC[r] = 0ull;
+      // chunks of 8 columns of both halves, software-pipelined: the loads of chunk c + 1
+      // are in flight while chunk c is evaluated (v[0..7] row / column t, v[8..15] row /
+      // column 128 + t)
+      tmem_ld8x2(tbase, tbase + kStream, vv[0]);
+      tmem_wait_ld(vv[0]);
 #pragma unroll
-      for (int c = 0; c < kSliceCols / 16; ++c) {
-        // 16 columns of both halves: v[0..15] row / column t, v[16..31] row / column 128 + t
-        uint32_t v[32];
-        tmem_ld16x2_wait(tbase + c * 16, tbase + kStream + c * 16, v);
+      for (int c = 0; c < kChunks; ++c) {
+        if (c + 1 < kChunks) tmem_ld8x2(tbase + (c + 1) * 8, tbase + kStream + (c + 1) * 8, vv[(c + 1) & 1]);
+        const uint32_t(&v)[16] = vv[c & 1];
 #pragma unroll
-        for (int p = 0; p < 8; ++p) {
-          const int col = h * kSliceCols + c * 16 + 2 * p;  // first column of the pair in the tile
+        for (int p = 0; p < 4; ++p) {
+          const int col = h * kSliceCols + c * 8 + 2 * p;  // first column of the pair in the tile
           const float4 qa = pr[col];
           const float4 qb = pr[col + 1];
           const uint64_t offA2 = pk(qa.x, qa.y), wA2 = pk(qa.z, qa.w);
 #pragma unroll
           for (int r = 0; r < 2; ++r) {
-            const uint64_t z2 = pk(__uint_as_float(v[16 * r + 2 * p]), __uint_as_float(v[16 * r + 2 * p + 1]));
-            const uint64_t vA = f2fma(alA2, z2, f2fma(ahA2, z2, f2add(ownA2[r], offA2)));
+            const uint64_t z2 = pk(__uint_as_float(v[8 * r + 2 * p]), __uint_as_float(v[8 * r + 2 * p + 1]));
+            const uint64_t vA = f2fma(ahA2, z2, f2add(ownA2[r], offA2));
             // G1: the inner column's dB from the pair data; G2: the own column's
             const uint64_t vB = f2fma(da2, z2, f2add(vA, ROWS ? pk(qb.x, qb.y) : ownD2[r]));
             const float2 vAf = upk(vA), vBf = upk(vB);
@@ -438,6 +451,7 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
             else accB[r] = f2fma(eB, pk(qb.z, qb.w), accB[r]);
           }
         }
+        if (c + 1 < kChunks) tmem_wait_ld(vv[(c + 1) & 1]);
       }
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
