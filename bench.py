@@ -50,6 +50,33 @@ def job_throughput(units_per_rank: float, local_seconds: float, dist=None, devic
     return world * float(units_per_rank) / sec, sec
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the sweeps from one
+# ncu capture of this bench's own command line, keyed by (workload, prec, n, d).  A figure is
+# reported only while the kernel source it was taken on is unchanged (sha256 of that file):
+# after any edit of the kernel the counters no longer describe it and `traffic` is null.
+NCU_TRAFFIC = {
+    ("highdim", "bf16_tc", 32768, 64): {
+        "source": "paper_2511_11359_gb300/csrc/lamp_tc.cu",
+        "sha256": "2468256b029e02d2fa1e6e9e3ffddd8c76deb95480b0b2d5ba2ceff4a931a976",
+        "row_sweep": 9221888, "col_sweep": 10008576},
+}
+
+
+def ncu_traffic(workload, prec, n, d, which):
+    import hashlib
+
+    rec = NCU_TRAFFIC.get((workload, prec, n, d))
+    if rec is None:
+        return None
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), rec["source"])
+    try:
+        with open(path, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    return rec[which] if digest == rec["sha256"] else None
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -389,7 +416,8 @@ def run_gpu(args, rank, world):
         achieved = n * m * 2 / (kern_ms[dom] / 1e3) / 1e12
         form = "tcgen05 x.y" if args.prec == "bf16_tc" else "f32x2 direct |x - y|^2"
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tex2/s", "frac": achieved / peak,
-                "traffic": None,
+                "traffic": ncu_traffic(args.workload, args.prec, n, w.d, "row_sweep" if dom == 0 else "col_sweep"),
+                "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "what": "MUFU ex2 of the " + ("row" if dom == 0 else "column") + f" sweep ({form}; 2 ex2 per entry: "
                         "streams A, B)",
                 "peak_source": f"{sms} SMs x {rate:.2f} ex2/clk/SM (measured, lamp_measure_ex2_rate) x {mhz:.0f} MHz"}
