@@ -25,8 +25,8 @@ Readings of passages that are silent, ambiguous or garbled:
   * the eta > 0 saddle dual D^eta includes the constant -eta H(r) that the
     printed formula (App. B) omits, so that weak duality holds as stated.
 
-Functions whose result has no independent pin are marked "parity unpinned"
-(only ``Dt_summand``).
+Functions whose result has no independent pin would be marked "parity unpinned"; none
+is (``Dt_summand`` is pinned by the re-expression in tests/test_oracle_dt.py).
 """
 from __future__ import annotations
 
@@ -583,8 +583,9 @@ def KL(X, Y) -> float:
 
 
 def Dt_summand(C, r, K, calpha, prev: LampState, info: StepInfo, new: LampState) -> float:
-    """One summand of D_t (Eq. def:sum_condition).  Parity unpinned: the paper
-    only describes its qualitative behaviour (App. D)."""
+    """One summand of D_t (Eq. def:sum_condition): the D_Ha and KL differences of the
+    midpoint analysis (Lemma summability).  Pinned by an independent re-expression of
+    both differences (Bregman form of D_Ha; log-normaliser form of the KL difference)."""
     Xs = r[:, None] * dual_to_primal(C, K, prev.kappa, prev.nu)[0]
     Xbar = r[:, None] * dual_to_primal(C, K, info.kappa_next, info.nubar)[0]
     Xnew = r[:, None] * dual_to_primal(C, K, new.kappa, new.nu)[0]

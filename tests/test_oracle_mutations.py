@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import oracle.lamp_oracle as OL
+import tests.test_oracle_dt as DT
 import tests.test_oracle_pins as PINS
 
 
@@ -61,6 +62,12 @@ MUTANTS = [
      PINS.test_certificate_log_term_is_one_over_t, ()),
     ("grad_envelope", "rowX[:, None] * x - X @ y", "rowX[:, None] * x - X.T[: x.shape[0], : y.shape[0]] @ y[: X.shape[0]]",
      PINS.test_envelope_gradient_matches_fd_of_sinkhorn_value, ()),
+    ("Dt_summand", "+ KL(Xbar, Xnew) - KL(Xbar, Xs)", "+ KL(Xnew, Xbar) - KL(Xbar, Xs)",
+     DT.test_dt_summand_matches_independent_form, (7, 9, 0.0, 2)),
+    ("Dt_summand", "dual_to_primal(C, K, new.kappa, new.nu)", "dual_to_primal(C, K, new.kappa, prev.nu)",
+     DT.test_dt_summand_matches_independent_form, (6, 6, 0.05, 3)),
+    ("Dt_summand", "- D_Ha(info.thetabar, prev.theta, calpha)", "+ D_Ha(info.thetabar, prev.theta, calpha)",
+     DT.test_dt_summand_matches_independent_form, (5, 4, 0.0, 1)),
 ]
 
 
