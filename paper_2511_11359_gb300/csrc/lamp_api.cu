@@ -205,6 +205,7 @@ __global__ void k_mark_done(DevState* dev) { dev->done = 1; }
 __global__ void k_set_state(DevState* dev, long long t, double kappa) {
   dev->t = t;
   dev->kappa = kappa;
+  dev->swf_kap = -1.0;  // the sweeps derive their constants until the next column finalize
   dev->done = 0;
   dev->status = 0;
   dev->ticket = 0u;
@@ -386,6 +387,7 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
     if (e != cudaSuccess) return bail(fail(ctx, LAMP_E_NOMEM, "cudaMallocHost: %s", cudaGetErrorString(e)));
   }
   std::memset(ctx->host_dev, 0, sizeof(DevState));
+  ctx->host_dev->swf_kap = -1.0;  // no cached sweep constants yet (kappa >= 0 always)
   ctx->host_dev->t_eval = -1;
   {
     cudaError_t e = cudaMemcpyAsync(w.dev, ctx->host_dev, sizeof(DevState), cudaMemcpyHostToDevice, ctx->stream);

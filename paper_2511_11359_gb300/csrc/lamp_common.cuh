@@ -50,8 +50,9 @@ constexpr double kLn2 = 0.69314718055994530942;
 
 enum CostKind : int { COST_DENSE = 0, COST_SQEUCLID = 1 };
 
-// threads per block of the O(n + m) finalize kernels (float64 math: more, smaller
-// blocks spread it over more SMs); rowred / colred hold one partial per block
+// threads per block of the O(n + m) finalize kernels; rowred / colred hold one partial
+// per block.  Their time is the float64 instruction latency of one thread's chain (the
+// FP64 rate of this part is ~1/64 of FP32), so smaller blocks do not make them faster.
 constexpr int kFinThreads = 128;
 inline int64_t fin_blocks(int64_t len) { return (len + kFinThreads - 1) / kFinThreads; }
 // doubles of Work::rscr: per-block partials of up to 4 + d fields for rows and columns,
@@ -231,6 +232,13 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
 #endif
 
 // Device-resident control block of one context.
+// float32 constants the sweeps take from make_sweep_params (a = ah + al per stream, and
+// a^B - a^A for the shared row shift)
+struct SweepF {
+  float ahA, alA, ahB, alB, dal;
+  float pad[3];
+};
+
 struct DevState {
   long long t;        // iteration index of the current state
   double kappa;       // kappa_t
@@ -249,7 +257,51 @@ struct DevState {
   double costA;       // <C, X^t>
   double colnu;       // <col(X^t), nu^t>
   double rlogZ;       // <r, log Z^t>
+  // the iteration's parameters at kappa = swf_kap (make_sweep_params of kappa_t and of
+  // kappa_{t+1}, and the sweeps' float32 constants), written once per iteration by the
+  // column finalize; swf_kap = -1 (never equal to kappa >= 0) until then
+  double swf_kap;
+  SweepF swf;
+  SweepParams spc, spn;
 };
+
+__host__ __device__ inline SweepF sweep_floats(const SweepParams& p) {
+  SweepF f;
+  f.ahA = p.ahA;
+  f.alA = p.alA;
+  f.ahB = p.ahB;
+  f.alB = p.alB;
+  f.dal = (float)(p.aB - p.aA);
+  f.pad[0] = f.pad[1] = f.pad[2] = 0.f;
+  return f;
+}
+
+#ifdef __CUDACC__
+// the sweeps' constants at the current kappa: from the control block when the column
+// finalize of the previous iteration computed them for this kappa, else (first iteration
+// after a state change, evaluation passes with a kappa override) derived here in float64
+__device__ __forceinline__ SweepF sweep_floats_of(const DevState* dev, const Consts& k) {
+  if (k.kap_ovr < 0.0 && !k.same_kappa) {
+    const double kap = dev->kappa;
+    if (dev->swf_kap == kap) return dev->swf;
+    return sweep_floats(make_sweep_params(kap, k));
+  }
+  return sweep_floats(make_sweep_params(sweep_kappa(dev->kappa, k), k));
+}
+
+// make_sweep_params of kappa_t and kappa_{t+1} for the finalize kernels (cached as above)
+__device__ __forceinline__ void iteration_params_of(const DevState* dev, const Consts& k, SweepParams& sp,
+                                                    SweepParams& spn) {
+  const double kap = dev->kappa;
+  if (k.kap_ovr < 0.0 && !k.same_kappa && dev->swf_kap == kap) {
+    sp = dev->spc;
+    spn = dev->spn;
+  } else {
+    sp = make_sweep_params(kap, k);
+    spn = make_sweep_params(sp.kapB, k);
+  }
+}
+#endif
 
 // Device buffers of one context (all owned by the context).
 struct Work {

@@ -122,9 +122,9 @@ k_pts_direct(const float* __restrict__ P_out, const float* __restrict__ P_in, in
     }
   }
 
-  const SweepParams sp = make_sweep_params(sweep_kappa(dev->kappa, k), k);
+  const SweepF sp = sweep_floats_of(dev, k);
   const uint64_t ahA2 = pk(sp.ahA, sp.ahA), alA2 = pk(sp.alA, sp.alA);
-  const float dal = (float)(sp.aB - sp.aA);  // a^B - a^A
+  const float dal = sp.dal;  // a^B - a^A
   const uint64_t da2 = pk(dal, dal);
 
   // own offsets: -RqA_i (row sweep), or -BqA_j and dB_j = BqA_j - BqB_j (column sweep)

@@ -25,6 +25,21 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// warp sum of float-float values (hi, lo): TwoSum of the high parts, low parts and their
+// errors added; the sweeps' per-thread sums are reduced in float32 arithmetic (the FP64
+// rate of this part is a small fraction of FP32) and converted once
+__device__ __forceinline__ void warp_sum_ff(float& hi, float& lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    float sum, err;
+    two_sum(hi, h2, sum, err);
+    hi = sum;
+    lo = lo + l2 + err;
+  }
+}
+
 __device__ __forceinline__ float warp_max_f(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -113,7 +128,7 @@ k_pts_sweep(const float* __restrict__ P_out, const float* __restrict__ P_in, int
   int64_t it1 = it0 + tiles_per_split;
   if (it1 > ntiles_in) it1 = ntiles_in;
 
-  SweepParams sp = make_sweep_params(sweep_kappa(dev->kappa, k), k);
+  const SweepF sp = sweep_floats_of(dev, k);
 
   stage_points(sOut, P_out, o0, n_out, d, tid, kThreads);
 
@@ -359,7 +374,7 @@ k_dense_rows(const float* __restrict__ C, int64_t ldc, int64_t n, int64_t m, con
   const int64_t c0 = (int64_t)split * chunks_per_split;
   int64_t c1 = c0 + chunks_per_split;
   if (c1 > nchunks) c1 = nchunks;
-  SweepParams sp = make_sweep_params(sweep_kappa(dev->kappa, k), k);
+  const SweepF sp = sweep_floats_of(dev, k);
   const float ahA = sp.ahA, alA = sp.alA, ahB = sp.ahB, alB = sp.alB;
 
   float oA[kDR], oB[kDR];
@@ -422,8 +437,10 @@ k_dense_rows(const float* __restrict__ C, int64_t ldc, int64_t n, int64_t m, con
   if (MODE == M_ROWSUM) {
 #pragma unroll
     for (int a = 0; a < kDR; ++a) {
-      double vA = warp_sum_d((double)hiA[a] + (double)loA[a]);
-      double vB = warp_sum_d((double)hiB[a] + (double)loB[a]);
+      warp_sum_ff(hiA[a], loA[a]);
+      warp_sum_ff(hiB[a], loB[a]);
+      const double vA = (double)hiA[a] + (double)loA[a];
+      const double vB = (double)hiB[a] + (double)loB[a];
       if (lane == 0) {
         sred[wid][2 * a] = vA;
         sred[wid][2 * a + 1] = vB;
@@ -474,7 +491,7 @@ k_dense_cols(const float* __restrict__ C, int64_t ldc, int64_t n, int64_t m, con
   const int64_t i0 = (int64_t)split * rows_per_split;
   int64_t i1 = i0 + rows_per_split;
   if (i1 > n) i1 = n;
-  SweepParams sp = make_sweep_params(sweep_kappa(dev->kappa, k), k);
+  const SweepF sp = sweep_floats_of(dev, k);
   const float ahA = sp.ahA, alA = sp.alA, ahB = sp.ahB, alB = sp.alB;
 
   float oA[4], oB[4];
@@ -682,9 +699,12 @@ k_row_fin(const Work w, int splits, const double* __restrict__ r, const Consts k
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double contrib = 0.0;
   if (i < k.n) {
-    SweepParams sp = make_sweep_params(dev->kappa, k);
-    SweepParams spn = make_sweep_params(sp.kapB, k);
+    SweepParams sp, spn;
+    iteration_params_of(dev, k, sp, spn);
     double SA = 0.0, SB = 0.0;
+    // unrolled: the partials' loads are independent and in flight together; the sums keep
+    // the split order
+#pragma unroll 8
     for (int s = 0; s < splits; ++s) {
       SA += rowpart[((int64_t)s * 2 + 0) * k.n + i];
       SB += rowpart[((int64_t)s * 2 + 1) * k.n + i];
@@ -745,12 +765,16 @@ k_col_fin(const Work w, int splits, const double* __restrict__ cvec, int rowbloc
   __shared__ bool amLast;
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double res = 0.0, cost = 0.0, cnu = 0.0;
-  SweepParams sp = make_sweep_params(dev->kappa, k);
+  SweepParams sp, spn;
+  iteration_params_of(dev, k, sp, spn);
   const int eval_only = dev->eval_only;
   if (j < k.m) {
     double aA = 0.0, aB = 0.0, aC = 0.0;
     // partials of split s: [s][3][m] with the cost-weighted sums, [s][2][m] without
     const int na = with_cost ? 3 : 2;
+    // unrolled: the partials' loads are independent and in flight together; the sums keep
+    // the split order
+#pragma unroll 8
     for (int s = 0; s < splits; ++s) {
       aA += colpart[((int64_t)s * na + 0) * k.m + j];
       aB += colpart[((int64_t)s * na + 1) * k.m + j];
@@ -785,7 +809,6 @@ k_col_fin(const Work w, int splits, const double* __restrict__ cvec, int rowbloc
       nu_nxt[j] = nun;
       th_nxt[j] = thn;
       // column data of iteration t+1
-      SweepParams spn = make_sweep_params(sp.kapB, k);
       const double wn = k.tau1 / spn.kapB;
       const double nbn = nun + wn * (thn - nun);         // nubar^{t+2}
       const double sny = k.zdot ? k.s * ny[j] : 0.0;
@@ -853,6 +876,14 @@ k_col_fin(const Work w, int splits, const double* __restrict__ cvec, int rowbloc
       dev->t = dev->t + 1;
       dev->kappa = sp.kapB;
       dev->cur ^= 1;
+      if (k.kap_ovr < 0.0 && !k.same_kappa) {
+        // the next iteration's parameters, once per iteration instead of once per thread
+        // (float64 is slow on this part)
+        dev->spc = spn;
+        dev->spn = make_sweep_params(spn.kapB, k);
+        dev->swf = sweep_floats(spn);
+        dev->swf_kap = spn.kapA;
+      }
     }
     __threadfence();
   }

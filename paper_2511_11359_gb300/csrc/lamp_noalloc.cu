@@ -64,6 +64,7 @@ __global__ void k_noalloc_init(lamp::DevState* dev, double kappa, const double* 
   if (j == 0) {
     dev->t = 0;
     dev->kappa = kappa;
+    dev->swf_kap = -1.0;
     dev->cur = 0;
     dev->done = 0;
     dev->status = 0;

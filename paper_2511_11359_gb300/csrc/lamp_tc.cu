@@ -370,12 +370,12 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
     // ---- epilogue: warps 0 .. kEpiWarps-1; TMEM lane t of both halves, column slice h ----
     const int t = (warp & 3) * 32 + lane;  // TMEM lane (0..127); rows t and 128 + t of the fixed tile
     const int h = warp >> 2;               // columns [h kSliceCols, (h + 1) kSliceCols) of each streamed tile
-    const SweepParams sp = make_sweep_params(sweep_kappa(dev->kappa, k), k);
+    const SweepF sp = sweep_floats_of(dev, k);
     // v^A = a^A z + own + off with a^A rounded to float32 (ah): dropping the low part al
     // changes v by at most half an ulp of a^A z, the order of the rounding of z itself in
     // the MMA's FP32 accumulation (the float32 CUDA-core paths keep al)
     const uint64_t ahA2 = pk(sp.ahA, sp.ahA);
-    const float dal = (float)(sp.aB - sp.aA);  // stream B: v^B = (a^B - a^A) z + (v^A + dB)
+    const float dal = sp.dal;  // stream B: v^B = (a^B - a^A) z + (v^A + dB)
     const uint64_t da2 = pk(dal, dal);
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;  // TMEM lane field
     // the own offsets of this thread's two fixed points (G1: the rows' shifts; G2: the
