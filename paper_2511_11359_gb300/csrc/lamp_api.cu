@@ -54,6 +54,7 @@ struct lamp_ctx {
   alignas(64) unsigned char map_y[128];
   alignas(64) unsigned char map_x64[128];
   alignas(64) unsigned char map_y64[128];
+  alignas(64) unsigned char map_c[128];  // stored cost (TMA-fed sweeps)
   std::string err;
 };
 
@@ -343,6 +344,16 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
     int min_inner = k.kind == LAMP_COST_DENSE ? 2 : 4;
     g.rows_split = choose_split(to, ti, (int64_t)g.sms * bpr, min_inner);
     g.cols_split = choose_split(tco, tci, (int64_t)g.sms * bpc, k.kind == LAMP_COST_DENSE ? 4 : min_inner);
+    if (k.kind == LAMP_COST_DENSE && dense_make_map(ctx->map_c, in.C, k.n, k.m, in.ldc) == cudaSuccess &&
+        dense_prepare() == cudaSuccess) {
+      // a stored cost with a 16-byte aligned base and rows a multiple of 16 bytes apart:
+      // the TMA-fed sweeps (32 x 256 tiles), at least 8 tiles per CTA for the copy ring
+      g.map_c = ctx->map_c;
+      const int64_t tr = dense_tile_rows(), tcl = dense_tile_cols();
+      const int64_t wave = (int64_t)g.sms * dense_blocks_per_sm();
+      g.rows_split = choose_split((k.n + tr - 1) / tr, (k.m + tcl - 1) / tcl, wave, 8);
+      g.cols_split = choose_split((k.m + tcl - 1) / tcl, (k.n + tr - 1) / tr, wave, 8);
+    }
   }
 
   // workspace
@@ -354,20 +365,22 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
   // the transport map widens the buffers on first use (ensure_part_width)
   const size_t gradd = k.kind == COST_SQEUCLID ? (size_t)std::min<int64_t>(std::max<int64_t>(k.d, 2), 8) : 2;
   ctx->part_width = (int)std::max<size_t>(3, gradd);
-  // column / row data are padded to whole tiles of every sweep (tc_pad: a multiple of 128;
-  // padding entries contribute nothing)
+  // the bf16 point copies are padded to whole 128-point units (tc_pad); the per-point
+  // column / row data to whole tiles of every sweep (a multiple of 256: the stored-cost
+  // row sweep reads the data of 256 columns per tile); padding entries contribute nothing
   const size_t m_pad = (size_t)tc_pad(k.m), n_pad = (size_t)tc_pad(k.n);
+  const size_t pm_pad = (m_pad + 255) / 256 * 256, pn_pad = (n_pad + 255) / 256 * 256;
   for (int b = 0; b < 2; ++b) {
     if ((rc = dalloc(ctx, &w.nu[b], m))) return bail(rc);
     if ((rc = dalloc(ctx, &w.theta[b], m))) return bail(rc);
-    if ((rc = dalloc(ctx, &w.colq[b], m_pad))) return bail(rc);
+    if ((rc = dalloc(ctx, &w.colq[b], pm_pad))) return bail(rc);
     if ((rc = dalloc(ctx, &w.rowshift[b], n))) return bail(rc);
   }
-  if ((rc = dalloc(ctx, &w.g2row, n_pad))) return bail(rc);
+  if ((rc = dalloc(ctx, &w.g2row, pn_pad))) return bail(rc);
   if (ctx->prec == LAMP_PREC_BF16_TC || k.shared_shift) {
     for (int b = 0; b < 2; ++b)
-      if ((rc = dalloc(ctx, &w.colq2[b], m_pad))) return bail(rc);
-    if ((rc = dalloc(ctx, &w.g2row2, n_pad))) return bail(rc);
+      if ((rc = dalloc(ctx, &w.colq2[b], pm_pad))) return bail(rc);
+    if ((rc = dalloc(ctx, &w.g2row2, pn_pad))) return bail(rc);
   }
   if ((rc = dalloc(ctx, &w.rowpart, (size_t)g.rows_split * ctx->part_width * n))) return bail(rc);
   if ((rc = dalloc(ctx, &w.colpart, (size_t)g.cols_split * ctx->part_width * m))) return bail(rc);
@@ -392,13 +405,13 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
   {
     cudaError_t e = cudaMemcpyAsync(w.dev, ctx->host_dev, sizeof(DevState), cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return bail(fail(ctx, LAMP_E_CUDA, "init copy: %s", cudaGetErrorString(e)));
-    tc_fill_pads(w.colq[0], k.m, (int64_t)m_pad, ctx->stream);
-    tc_fill_pads(w.colq[1], k.m, (int64_t)m_pad, ctx->stream);
-    tc_fill_pads(w.g2row, k.n, (int64_t)n_pad, ctx->stream);
+    tc_fill_pads(w.colq[0], k.m, (int64_t)pm_pad, ctx->stream);
+    tc_fill_pads(w.colq[1], k.m, (int64_t)pm_pad, ctx->stream);
+    tc_fill_pads(w.g2row, k.n, (int64_t)pn_pad, ctx->stream);
     if (w.g2row2) {
-      tc_fill_pairs(w.colq2[0], (int64_t)m_pad, ctx->stream);
-      tc_fill_pairs(w.colq2[1], (int64_t)m_pad, ctx->stream);
-      tc_fill_pairs(w.g2row2, (int64_t)n_pad, ctx->stream);
+      tc_fill_pairs(w.colq2[0], (int64_t)pm_pad, ctx->stream);
+      tc_fill_pairs(w.colq2[1], (int64_t)pm_pad, ctx->stream);
+      tc_fill_pairs(w.g2row2, (int64_t)pn_pad, ctx->stream);
     }
     cudaMemsetAsync(w.nu[0], 0, m * sizeof(double), ctx->stream);
     cudaMemsetAsync(w.theta[0], 0, m * sizeof(double), ctx->stream);

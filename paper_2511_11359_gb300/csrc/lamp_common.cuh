@@ -229,6 +229,21 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
   hi = s;
   lo += e;
 }
+
+// warp sum of float-float values (hi, lo): TwoSum of the high parts, low parts and their
+// errors added; the sweeps' per-thread sums are reduced in float32 arithmetic (the FP64
+// rate of this part is a small fraction of FP32) and converted once
+__device__ __forceinline__ void warp_sum_ff(float& hi, float& lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    float sum, err;
+    two_sum(hi, h2, sum, err);
+    hi = sum;
+    lo = lo + l2 + err;
+  }
+}
 #endif
 
 // Device-resident control block of one context.
@@ -339,6 +354,7 @@ struct Geometry {
   const void* map_y;  // 128-row boxes (fixed tiles) ...
   const void* map_x64;  // ... and 64-row boxes (streamed tiles)
   const void* map_y64;
+  const void* map_c;  // tensor map of a stored cost for the TMA-fed sweeps (LAMP_COST_DENSE), else null
   int sms;
   int rows_split;   // inner splits of the row sweep
   int cols_split;   // inner splits of the column sweep
@@ -377,6 +393,14 @@ cudaError_t tc_convert(const float* P, int64_t np, int d, float* Pr, void* Pb, c
 cudaError_t tc_fill_pads(float4* a, int64_t from, int64_t to, cudaStream_t st);
 cudaError_t tc_fill_pairs(float4* a, int64_t count, cudaStream_t st);
 cudaError_t tc_make_map(void* map_out, const void* base, int64_t rows_pad, int box_rows);
+// stored-cost sweeps fed by TMA (lamp_dense.cu)
+cudaError_t dense_make_map(void* map_out, const float* C, int64_t n, int64_t m, int64_t ldc);
+cudaError_t dense_prepare();
+int dense_tile_rows();
+int dense_tile_cols();
+int dense_blocks_per_sm();
+cudaError_t dense_launch_sweep(bool rows, int eval, const Geometry& g, const Work& w, const Consts& k, int splits,
+                               cudaStream_t st);
 int tc_tile_fixed();   // points of the fixed tile of a tensor-core sweep
 int tc_tile_stream();  // points of a streamed tile
 cudaError_t tc_prepare();

@@ -25,21 +25,6 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// warp sum of float-float values (hi, lo): TwoSum of the high parts, low parts and their
-// errors added; the sweeps' per-thread sums are reduced in float32 arithmetic (the FP64
-// rate of this part is a small fraction of FP32) and converted once
-__device__ __forceinline__ void warp_sum_ff(float& hi, float& lo) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-    float sum, err;
-    two_sum(hi, h2, sum, err);
-    hi = sum;
-    lo = lo + l2 + err;
-  }
-}
-
 __device__ __forceinline__ float warp_max_f(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -994,6 +979,7 @@ cudaError_t launch_init_state(const Inputs& in, const Consts& k, const Work& w, 
 
 static cudaError_t launch_row_sweep(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int mode,
                                     cudaStream_t st) {
+  if (k.kind == COST_DENSE && g.map_c && mode == M_ROWSUM) return dense_launch_sweep(true, 0, g, w, k, g.rows_split, st);
   if (k.kind == COST_DENSE) {
     int64_t nch = cdiv(k.m, kDChunk);
     int cps = (int)cdiv(nch, g.rows_split);
@@ -1018,6 +1004,9 @@ static cudaError_t launch_row_sweep(const Inputs& in, const Consts& k, const Wor
 
 static cudaError_t launch_col_sweep(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int eval,
                                     cudaStream_t st) {
+  // stored costs accumulate <C, X^t> in every iteration (the column finalize reads three
+  // partials per split whenever the row shift is not shared)
+  if (k.kind == COST_DENSE && g.map_c) return dense_launch_sweep(false, 1, g, w, k, g.cols_split, st);
   if (k.kind == COST_DENSE) {
     int64_t rps = cdiv(k.n, g.cols_split);
     rps = cdiv(rps, kDColRows) * kDColRows;

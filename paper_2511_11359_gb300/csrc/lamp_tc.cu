@@ -30,6 +30,7 @@
 #include <cmath>
 #include <cstdint>
 
+#include "lamp_async.cuh"
 #include "lamp_common.cuh"
 
 namespace lamp {
@@ -56,8 +57,8 @@ constexpr int kProducerWarp = kEpiWarps;
 constexpr int kMmaWarp = kEpiWarps + 1;
 constexpr int kThreads = (kEpiWarps + 2) * 32;
 constexpr uint32_t kTmemCols = 256;         // two buffers x two 64-column FP32 accumulators
-constexpr uint32_t kWaitLimit = 1u << 24;   // bounded spin on every mbarrier
-constexpr int kTimeoutStatus = 6;           // LAMP_E_TIMEOUT
+constexpr uint32_t kWaitLimit = async::kWaitLimit;  // bounded spin on every mbarrier
+constexpr int kTimeoutStatus = async::kTimeoutStatus;
 
 struct __align__(8) Bars {
   uint64_t fixed_full;
@@ -73,67 +74,19 @@ struct __align__(8) Bars {
 constexpr int kBarBytes = 256;
 static_assert(sizeof(Bars) <= kBarBytes, "barrier block");
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+using async::bulk_load;
+using async::fence_proxy_async_smem;
+using async::mbar_arrive;
+using async::mbar_drain;
+using async::mbar_expect_tx;
+using async::mbar_init;
+using async::smem_u32;
+using async::tma_load_2d;
 
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n"
-      ".reg .pred p;\n"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      "selp.u32 %0, 1, 0, p;\n"
-      "}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// bounded wait; false when the CTA is in error or the limit ran out (then the error is recorded)
+// bounded wait on one of this CTA's barriers (error flag in the barrier block)
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, Bars* B, DevState* dev,
-                                          uint32_t limit = kWaitLimit) {
-  for (uint32_t it = 0; it < limit; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (*(volatile int*)&B->err) return false;
-  }
-  atomicExch(&B->err, 1);
-  atomicExch(&dev->status, kTimeoutStatus);
-  return false;
-}
-
-// drain wait used on the error path: only the iteration limit, no early exit
-__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < kWaitLimit; ++it)
-    if (mbar_try_wait(bar, parity)) return;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
-          "r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
-      : "memory");
-}
-
-// plain (untiled) bulk copy global -> shared, completion counted on an mbarrier;
-// both addresses 16-byte aligned, size a multiple of 16
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
+                                          uint32_t limit = async::kWaitLimit) {
+  return async::mbar_wait(bar, parity, &B->err, dev, limit);
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
@@ -155,11 +108,6 @@ __device__ __forceinline__ void tc_fence_before() {
 
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// orders this thread's generic-proxy accesses of shared memory before later async-proxy
-// accesses (bulk copies) that other threads issue after synchronising with it
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 
 // D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (bf16 in, fp32 accumulate)
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -294,7 +242,7 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
       mbar_init(&B->pair_empty[b], kEpiThreads);
     }
     B->err = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    async::mbar_init_fence();
   }
   if (warp == 0) {
     tmem_alloc(&B->tmem_base, kTmemCols);
@@ -552,7 +500,7 @@ __global__ void k_wait_selftest(uint32_t limit, DevState* dev) {
   if (threadIdx.x == 0) {
     mbar_init(&B.full[0], 1);
     B.err = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    async::mbar_init_fence();
   }
   __syncthreads();
   if (threadIdx.x == 0) {

@@ -47,9 +47,13 @@ def test_trajectory_points(case):
 
 
 DENSE_CASES = [
+    # rows 16-byte multiples apart (m % 4 == 0) take the TMA-fed sweeps (32 x 256 tiles):
+    # grid16, dense_rand_eta and dense_tma_ragged (ragged row blocks and column tiles);
+    # m = 1029 takes the plain-load sweeps
     ("grid16", "grid", 16, 1e-3),
     ("dense_rand", "rand", (173, 1029), 0.0),
     ("dense_rand_eta", "rand", (64, 2100), 5e-2),
+    ("dense_tma_ragged", "rand", (300, 1100), 0.0),
 ]
 
 
@@ -73,6 +77,46 @@ def test_trajectory_dense(case):
         st_ref = O.lamp_run(C, w.r, w.c, P, T - done, state=st_ref)
         done = T
         assert_pot_close(s.get_state(), st_ref, what=f"{name} T={T}")
+    s.close()
+
+
+@pytest.mark.parametrize("n,m", [(1024, 512), (64, 4096), (1000, 4100)])
+def test_dense_split_sweeps(n, m):
+    """Stored costs whose TMA-fed sweeps split the inner dimension over several CTAs:
+    1024 x 512 (column sweep: 4 row splits), 64 x 4096 (row sweep: 2 column splits),
+    1000 x 4100 (both, ragged)."""
+    w = W.dense_problem("sp", n, m, seed=n + m)
+    s, C, K = gpu_solver(w, check_every=5)
+    P = O.LampParams(K=K)
+    done, st_ref = 0, None
+    for T in (1, 10, 30):
+        s.iterate(T - done)
+        st_ref = O.lamp_run(C, w.r, w.c, P, T - done, state=st_ref)
+        done = T
+        assert_pot_close(s.get_state(), st_ref, what=f"dense split {n}x{m} T={T}")
+    s.close()
+
+
+@pytest.mark.parametrize("ldc", [304, 301])
+def test_dense_with_leading_dimension(ldc):
+    """C as an n x m view of a wider row-major array: ldc = 304 keeps rows 16-byte multiples
+    apart (TMA-fed sweeps), ldc = 301 does not (plain-load sweeps); both match the oracle on
+    the n x m cost."""
+    import torch
+
+    w = W.dense_problem("ld", 257, 300, seed=5)
+    wide = np.zeros((w.n, ldc), dtype=np.float32)
+    wide[:, : w.m] = w.C
+    wide[:, w.m:] = 7.0  # never read
+    Cd = torch.from_numpy(wide).cuda()[:, : w.m]
+    C, _, K = oracle_cost(w)
+    import paper_2511_11359_gb300 as L
+
+    s = L.Lamp(dev(w.r), dev(w.c), C=Cd, K=K, check_every=4)
+    T = 30
+    s.iterate(T)
+    ref = O.lamp_run(C, w.r, w.c, O.LampParams(K=K), T)
+    assert_pot_close(s.get_state(), ref, what=f"dense ldc={ldc}")
     s.close()
 
 
