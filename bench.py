@@ -57,8 +57,12 @@ def job_throughput(units_per_rank: float, local_seconds: float, dist=None, devic
 NCU_TRAFFIC = {
     ("highdim", "bf16_tc", 32768, 64): {
         "source": "paper_2511_11359_gb300/csrc/lamp_tc.cu",
-        "sha256": "2468256b029e02d2fa1e6e9e3ffddd8c76deb95480b0b2d5ba2ceff4a931a976",
-        "row_sweep": 9221888, "col_sweep": 10008576},
+        "sha256": "7ab7588b802af7425939fad61349b35e6c75407a6212a2ef545656fe7ccc9ef2",
+        "row_sweep": 9223424, "col_sweep": 10010368},
+    ("image_grid", "fp32", 4096, 0): {
+        "source": "paper_2511_11359_gb300/csrc/lamp_dense.cu",
+        "sha256": "0214d7ff91ff3f635ac75b39f297454933f9a9a9becf2116f747fecebaf78424",
+        "row_sweep": 67254016 + 217088, "col_sweep": 67259648 + 328960},
 }
 
 
@@ -407,7 +411,9 @@ def run_gpu(args, rank, world):
     if bytes_per_entry:
         achieved = n * m * bytes_per_entry / (kern_ms[dom] / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "frac": achieved / peaks["hbm_gbs"],
+                "traffic": ncu_traffic(args.workload, args.prec, n, w.d, "row_sweep" if dom == 0 else "col_sweep"),
+                "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "what": "stored C bytes of the " + ("row" if dom == 0 else "column") + " sweep"}
     elif args.prec == "bf16_tc" or w.d <= 8:
         # tensor-core sweeps, and the packed f32x2 direct-form sweeps (d <= 8): two ex2 per entry
