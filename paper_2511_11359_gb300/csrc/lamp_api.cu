@@ -340,10 +340,16 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
     g.rows_tiles = (int)to;
     g.cols_tiles = (int)tco;
     // at least 4 inner tiles per CTA (dense rows: 2 chunks of 1024 columns), so that a
-    // CTA's fixed costs (parameters, reduction) stay small against its sweep
+    // CTA's fixed costs (parameters, reduction) stay small against its sweep; a problem
+    // whose grid would not fill a quarter of one wave takes one tile per CTA instead
+    // (n = m = 256 points: 2 CTAs instead of 1 per sweep)
     int min_inner = k.kind == LAMP_COST_DENSE ? 2 : 4;
-    g.rows_split = choose_split(to, ti, (int64_t)g.sms * bpr, min_inner);
-    g.cols_split = choose_split(tco, tci, (int64_t)g.sms * bpc, k.kind == LAMP_COST_DENSE ? 4 : min_inner);
+    const auto mi = [&](int64_t tout, int64_t tin, int64_t wave, int base) {
+      return tout * std::max<int64_t>(tin / base, 1) * 4 < wave ? 1 : base;
+    };
+    g.rows_split = choose_split(to, ti, (int64_t)g.sms * bpr, mi(to, ti, (int64_t)g.sms * bpr, min_inner));
+    g.cols_split = choose_split(tco, tci, (int64_t)g.sms * bpc,
+                                mi(tco, tci, (int64_t)g.sms * bpc, k.kind == LAMP_COST_DENSE ? 4 : min_inner));
     if (k.kind == LAMP_COST_DENSE && dense_make_map(ctx->map_c, in.C, k.n, k.m, in.ldc) == cudaSuccess &&
         dense_prepare() == cudaSuccess) {
       // a stored cost with a 16-byte aligned base and rows a multiple of 16 bytes apart:
