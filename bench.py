@@ -421,22 +421,27 @@ def run_gpu(args, rank, world):
         peak = sms * rate * mhz * 1e6 / 1e12
         achieved = n * m * 2 / (kern_ms[dom] / 1e3) / 1e12
         form = "tcgen05 x.y" if args.prec == "bf16_tc" else "f32x2 direct |x - y|^2"
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tex2/s", "frac": achieved / peak,
-                "traffic": ncu_traffic(args.workload, args.prec, n, w.d, "row_sweep" if dom == 0 else "col_sweep"),
-                "traffic_unit": "bytes per launch (ncu dram read + write)",
+        mufu = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tex2/s", "frac": achieved / peak,
                 "what": "MUFU ex2 of the " + ("row" if dom == 0 else "column") + f" sweep ({form}; 2 ex2 per entry: "
                         "streams A, B)",
                 "peak_source": f"{sms} SMs x {rate:.2f} ex2/clk/SM (measured, lamp_measure_ex2_rate) x {mhz:.0f} MHz"}
-        if args.prec != "bf16_tc":
-            # float32 lane operations per entry of a regular iteration: d sub + d mul/fma (cost);
-            # stream A add + 2 fma (compensated exponent) + fma (weighted sum); stream B, through
-            # the shared row shift, add + fma + fma
+        if args.prec == "bf16_tc":
+            # MUFU binds: 16 entries / clk / SM, against ~21 for the FP32 pipe at 6 lane-ops per entry
+            roof = dict(mufu)
+        else:
+            # the FP32 pipe binds the direct form: float32 lane operations per entry of a regular
+            # iteration: d sub + d mul/fma (cost); stream A add + 2 fma (compensated exponent) +
+            # fma (weighted sum); stream B, through the shared row shift, add + fma + fma; at d = 3
+            # that is 13 lane-ops, 9.8 entries / clk / SM, against 16 for MUFU
             lanes = 2 * w.d + 7
             fpeak = sms * 128 * mhz * 1e6 / 1e12
             fach = n * m * lanes / (kern_ms[dom] / 1e3) / 1e12
-            roof["fp32_pipe"] = {"lane_ops_per_entry": lanes, "achieved": fach, "peak": fpeak, "unit": "Tlane-op/s",
-                                 "frac": fach / fpeak,
-                                 "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz"}
+            roof = {"bound": "alu", "achieved": fach, "peak": fpeak, "unit": "Tlane-op/s", "frac": fach / fpeak,
+                    "what": "FP32-pipe lane operations of the " + ("row" if dom == 0 else "column") +
+                            f" sweep ({form}; {lanes} lane-ops per entry)",
+                    "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz", "mufu": mufu}
+        roof["traffic"] = ncu_traffic(args.workload, args.prec, n, w.d, "row_sweep" if dom == 0 else "col_sweep")
+        roof["traffic_unit"] = "bytes per launch (ncu dram read + write)"
     else:
         peak = sms * 128 * 2 * mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flop x max SM clock
         achieved = n * m * flops_per_entry / (kern_ms[dom] / 1e3) / 1e12
