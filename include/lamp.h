@@ -83,7 +83,9 @@ typedef enum {
  *   d         point dimension of the point-cloud kinds (1 <= d <= 64); ignored for DENSE.
  *   kind      lamp_cost_kind.
  *   C, ldc    DENSE: row-major n x m float32, entry (i,j) at C[i*ldc + j], ldc >= m,
- *             entries >= 0 and finite (C in R_+^{n x m}, Alg. 2).
+ *             entries >= 0 and finite (C in R_+^{n x m}, Alg. 2).  With C 16-byte
+ *             aligned and ldc a multiple of 4 the sweeps stream C by tensor (TMA)
+ *             copies; otherwise by plain loads (same results up to rounding).
  *   x, y      point-cloud kinds: row-major n x d and m x d float32 point coordinates.
  *   r, c      float64 marginals, entries > 0, each summing to 1 within 1e-9
  *             (r in Delta^n, c in Delta^m with full support, Lemma l1_prob_equiv).
