@@ -24,6 +24,8 @@ CASES = [
     ("pts3_eta", "points", 1500, 1100, 3, 0.05, "fp32", 25),
     ("dense", "dense", 290, 1100, 0, 0.0, "fp32", 30),
     ("dense_eta", "dense", 700, 300, 0, 0.02, "fp32", 20),
+    # stored cost whose TMA-fed column sweep splits its rows over 4 CTAs per column block
+    ("dense_split", "dense", 1024, 512, 0, 0.0, "fp32", 20),
     ("dot16", "points", 400, 300, 16, 0.0, "fp32", 30),
     ("tc64", "points", 384, 300, 64, 0.0, "bf16_tc", 30),
 ]
