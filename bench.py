@@ -239,7 +239,10 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / it, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        # the GPU arm's config keys, with the precision and the sample of this arm
         "config": {"workload": args.workload, "n": w.n, "m": w.m, "d": w.d, "eta": w.eta,
+                   "prec": "f64 (NumPy oracle)", "cost": w.kind, "l2": "not applicable (host)",
+                   "parallelism": "host, 1 thread",
                    "sample": f"{min(w.n, args.cpu_points)}x{min(w.m, args.cpu_points)}"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
