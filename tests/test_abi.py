@@ -59,6 +59,10 @@ BAD = [
     ({}, {"eta": -1.0}), ({}, {"alpha": 0.0}), ({}, {"beta": -0.1}), ({}, {"tau1": -1.0}),
     ({}, {"tau1": 2.0, "eta": 1.0}), ({}, {"check_every": 0}), ({}, {"max_iter": -5}), ({}, {"prec": 9}),
     ({}, {"K": -1.0}), ({}, {"tol": float("nan")}), ({}, {"eta": float("inf")}),
+    # tensor cores only for the dot-form costs (LAMP_COST_L1 = 2, LAMP_COST_LINF = 3, DENSE = 0)
+    ({"kind": 2}, {"prec": 1}), ({"kind": 3}, {"prec": 1}), ({"kind": 0, "C": 0x10, "ldc": 9}, {"prec": 1}),
+    ({"n": 1 << 32}, {}), ({"m": (1 << 31) + 1}, {}), ({}, {"check_every": 100001}),
+    ({"cost_scale": float("inf")}, {}), ({}, {"alpha": float("nan")}), ({}, {"K": float("inf")}),
 ]
 
 
