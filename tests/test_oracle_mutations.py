@@ -13,6 +13,7 @@ import pytest
 
 import oracle.lamp_oracle as OL
 import tests.test_oracle_dt as DT
+import tests.test_oracle_golden as GOLD
 import tests.test_oracle_pins as PINS
 
 
@@ -68,6 +69,10 @@ MUTANTS = [
      DT.test_dt_summand_matches_independent_form, (6, 6, 0.05, 3)),
     ("Dt_summand", "- D_Ha(info.thetabar, prev.theta, calpha)", "+ D_Ha(info.thetabar, prev.theta, calpha)",
      DT.test_dt_summand_matches_independent_form, (5, 4, 0.0, 1)),
+    ("eot_value", "- eta * entropy(X)", "+ eta * entropy(X)",
+     GOLD.test_sinkhorn_plan_and_value_equal_closed_form, (GOLD.FIX["entropic"][0],)),
+    ("entropy", "np.log(Xp)", "np.log2(Xp)",
+     GOLD.test_sinkhorn_plan_and_value_equal_closed_form, (GOLD.FIX["entropic"][0],)),
 ]
 
 
