@@ -119,27 +119,43 @@ typedef struct {
  *   max_iter   lamp_solve stops at iteration index t = max_iter at the latest.
  *   check_every how many iterations run on the device between host polls (>= 1).
  *   prec       lamp_precision (SQEUCLID only).
+ *   infeas_only for eta > 0: 0 (default) stops on infeasibility only once also
+ *              1 - kappa_t eta <= tol (X^t then solves the eta problem, not the eta_t one);
+ *              1 stops on infeasibility alone.  Ignored for eta = 0.
  *   K          0: ||C||_inf computed on the device from the cost the kernels use;
  *              > 0: use this value for K.
+ *   gap_tol    > 0: lamp_solve also stops at the first evaluated X^t whose primal-dual
+ *              gap P^eta(X^t) - max(D(theta^t), D(nu^t)) of the saddle problem is <= gap_tol
+ *              (App. B duals, App. E.2 termination); 0: no gap test.
+ *   gap_every  iterations between gap evaluations (0 means check_every); each costs one
+ *              evaluation pass and the dual sweeps of lamp_dual.
  */
 typedef struct {
   double eta, tau1, tau2, alpha, beta, tol;
   int64_t max_iter, check_every;
   int32_t prec;
-  int32_t _pad0;
+  int32_t infeas_only;
   double K;
+  double gap_tol;
+  int64_t gap_every;
 } lamp_params;
 
 /* Summary of the current state (all host values).
  *   iters    iteration index t of the state (number of updates applied).
  *   infeas   ||col(X^t) - c||_1 + ||row(X^t) - r||_1 (float64 sums).
  *   obj_CX   <C, X^t>.
- *   kappa    1/eta_t.   K  the ||C||_inf in use.   status  LAMP_OK, LAMP_E_NOT_CONVERGED or LAMP_E_NUMERIC. */
+ *   kappa    1/eta_t.   K  the ||C||_inf in use.   status  LAMP_OK, LAMP_E_NOT_CONVERGED or LAMP_E_NUMERIC.
+ *   stop     why lamp_solve stopped: LAMP_STOP_INFEAS, LAMP_STOP_GAP or LAMP_STOP_MAX_ITER (0 otherwise).
+ *   gap      the last evaluated primal-dual gap (gap_tol > 0), else NaN. */
+#define LAMP_STOP_INFEAS 1
+#define LAMP_STOP_GAP 2
+#define LAMP_STOP_MAX_ITER 3
 typedef struct {
   int64_t iters;
   double infeas, obj_CX, kappa, K;
   int32_t status;
-  int32_t _pad0;
+  int32_t stop;
+  double gap;
 } lamp_result;
 
 /* Fill *p with the defaults listed above (tol = 1e-6, max_iter = 100000, check_every = 50). */
@@ -152,9 +168,10 @@ LAMP_API int lamp_params_default(lamp_params* p);
 LAMP_API int lamp_create(lamp_ctx** out, const lamp_problem* prob, const lamp_params* params, void* stream);
 
 /* Run Alg. 2 from the current state until the infeasibility of X^t is <= tol
- * or t reaches max_iter (App. E.2 termination, checked on X^t before the
- * iteration's updates).  The state left in the context is that X^t's state.
- * Returns LAMP_OK, LAMP_E_NOT_CONVERGED (max_iter reached; *out is valid),
+ * (for eta > 0 see infeas_only), or, with gap_tol > 0, until an evaluated X^t has a
+ * primal-dual gap <= gap_tol, or t reaches max_iter (App. E.2 termination, checked on
+ * X^t before the iteration's updates).  The state left in the context is that X^t's
+ * state.  Returns LAMP_OK, LAMP_E_NOT_CONVERGED (max_iter reached; *out is valid),
  * LAMP_E_NUMERIC or LAMP_E_CUDA.  out may be NULL. */
 LAMP_API int lamp_solve(lamp_ctx* ctx, lamp_result* out);
 
@@ -169,8 +186,14 @@ LAMP_API int lamp_iterate(lamp_ctx* ctx, int64_t iters);
  *   out[4] P^eta(X^t)           (Eq. prob:l1_ot_primal)
  *   out[5] certificate RHS 4K||col-c||_1 + 2K log m / t (Prop. infeas_bound (a); eta = 0, t >= 1, else NaN)
  *   out[6] saddle dual max(D(theta^t), D(nu^t)), as lamp_dual (two or four extra sweeps)
- *   out[7] K */
-LAMP_API int lamp_objective(lamp_ctx* ctx, double out[8]);
+ *   out[7] K
+ *   out[8] L = <C, X^t> - eta H(X^t), the entropic objective of Eq. prob:primal_eot at X^t (the
+ *          loss the autograd form returns; its gradient is lamp_grad's)
+ *   out[9] primal-dual gap out[4] - out[6] of the saddle problem (App. B, App. E.2), >= 0 up to
+ *          rounding by weak duality
+ * out must hold LAMP_OBJECTIVE_SLOTS doubles. */
+#define LAMP_OBJECTIVE_SLOTS 10
+LAMP_API int lamp_objective(lamp_ctx* ctx, double out[LAMP_OBJECTIVE_SLOTS]);
 
 /* Transport-map application (App. E, colour transfer): with the current
  * X^t = diag(r) p^{eta_t}(nu^t) and p row-stochastic,
@@ -189,9 +212,12 @@ LAMP_API int lamp_apply_map(lamp_ctx* ctx, const float* V, int64_t k, float* out
  *   D^eta(phi) = sum_i r_i softmin^eta_j (C_ij + 2K phi_j) - 2K <c, phi> - eta H(r)     (eta > 0)
  * at phi = theta^t (out[0]) and phi = nu^t (out[1]); host memory, synchronises.  For
  * any phi in [-1, 1]^m it is a lower bound on the optimal value of the penalised problem
- * (weak duality).  eta = 0: one row-max sweep per phi, evaluated in float32 with
- * offsets on the kernels' grid (absolute error about 1e-6 K); eta > 0: a row-max and a
- * row-sum sweep per phi at kappa = 1/eta.  The state is not changed. */
+ * (weak duality).  eta = 0: two row-max sweeps per phi at a large kappa, the second with
+ * the row shifts of the first and the sub-grid remainders of the column offsets
+ * subtracted, so the row minima of the kernels' float32 cost come out to about 1e-12 K
+ * (the float32 cost itself differs from an exact one by its own rounding); eta > 0: a
+ * row-max and a row-sum sweep per phi at kappa = 1/eta (relative error of the row sums
+ * about 2^-22, i.e. about 2^-22 eta in the softmin).  The state is not changed. */
 LAMP_API int lamp_dual(lamp_ctx* ctx, double out[2]);
 
 /* Round (Alg. 3, Altschuler et al.) of the current X^t, returned in factored form
@@ -285,8 +311,9 @@ LAMP_API const char* lamp_last_error(const lamp_ctx* ctx);
  * Scratch comes from a 16 MiB array compiled into the library (each GPU that
  * loads the library keeps it until the process exits).  Requests whose
  * workspace does not fit (about 136 n + 168 m bytes) return LAMP_E_INVALID.
- * The first call on a device looks up the array's device address; make it
- * before starting any stream capture.  All calls on a device share the array:
+ * The first call on a device looks up the array's device address (and looks it
+ * up again when it finds a different CUDA context current on that device, e.g.
+ * after cudaDeviceReset); make that call before starting any stream capture.  All calls on a device share the array:
  * calls whose GPU work overlaps (other streams, other threads) race and
  * corrupt each other, so issue them one after another on one stream.  The
  * array keeps the previous call's contents; the call clears what must start

@@ -475,7 +475,8 @@ def objective_report(C, r, c, K, eta, state: LampState) -> dict:
     H = entropy(X)
     out = {
         "cost": cost, "col_res": col_res, "row_res": row_res, "entropy": H,
-        "P_eta": cost + 2.0 * K * col_res - eta * H,
+        "P_eta": penalized_objective(X, C, c, K, eta),
+        "L": eot_value(C, X, eta),
         "certificate": certificate_rhs(K, col_res, C.shape[1], state.t) if (eta == 0.0 and state.t > 0) else float("nan"),
         "dual": max(saddle_dual(C, r, c, K, state.theta, eta), saddle_dual(C, r, c, K, state.nu, eta)),
         "K": K, "logZ": logZ, "col": colX, "X": X,

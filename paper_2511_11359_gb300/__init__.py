@@ -12,7 +12,7 @@ Entry points mirror include/lamp.h:
     Lamp(...)              lamp_create            (device tensors, borrowed)
     Lamp.solve()           lamp_solve             (run Alg. 2 to the tolerance)
     Lamp.iterate(k)        lamp_iterate           (exactly k iterations)
-    Lamp.objective()       lamp_objective         (<C,X>, residuals, H, P^eta, certificate, dual, K)
+    Lamp.objective()       lamp_objective         (<C,X>, residuals, H, P^eta, certificate, dual, K, L, gap)
     Lamp.dual()            lamp_dual              (saddle dual D at theta^t and nu^t)
     Lamp.round()           lamp_round             (Round(X^t) in factored form, its cost)
     Lamp.apply_map(V, side) lamp_apply_map        (p V or p^T U: transport-map application)
@@ -53,6 +53,7 @@ COST_COSINE = 4
 _POINT_COSTS = {"sqeuclid": COST_SQEUCLID, "l1": COST_L1, "linf": COST_LINF, "cosine": COST_COSINE}
 PREC_FP32 = 0
 PREC_BF16_TC = 1
+OBJECTIVE_SLOTS = 10  # LAMP_OBJECTIVE_SLOTS of lamp.h
 
 EXPORTED_SYMBOLS = [
     "lamp_params_default", "lamp_create", "lamp_solve", "lamp_iterate", "lamp_objective", "lamp_grad",
@@ -84,13 +85,17 @@ class _Params(ctypes.Structure):
     _fields_ = [("eta", ctypes.c_double), ("tau1", ctypes.c_double), ("tau2", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int64), ("check_every", ctypes.c_int64),
-                ("prec", ctypes.c_int32), ("_pad0", ctypes.c_int32), ("K", ctypes.c_double)]
+                ("prec", ctypes.c_int32), ("infeas_only", ctypes.c_int32), ("K", ctypes.c_double),
+                ("gap_tol", ctypes.c_double), ("gap_every", ctypes.c_int64)]
 
 
 class _Result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("infeas", ctypes.c_double), ("obj_CX", ctypes.c_double),
                 ("kappa", ctypes.c_double), ("K", ctypes.c_double), ("status", ctypes.c_int32),
-                ("_pad0", ctypes.c_int32)]
+                ("stop", ctypes.c_int32), ("gap", ctypes.c_double)]
+
+
+STOP_REASONS = {0: None, 1: "infeasibility", 2: "gap", 3: "max_iter"}
 
 
 def _load():
@@ -263,15 +268,16 @@ class Lamp:
         ok = (LAMP_OK, LAMP_E_NOT_CONVERGED) if allow_not_converged else (LAMP_OK,)
         code = _check(_get_lib().lamp_solve(self._h, ctypes.byref(res)), self._h, ok)
         return {"iters": int(res.iters), "infeas": res.infeas, "cost": res.obj_CX, "kappa": res.kappa,
-                "K": res.K, "status": int(res.status), "converged": code == LAMP_OK}
+                "K": res.K, "status": int(res.status), "converged": code == LAMP_OK,
+                "stop": STOP_REASONS.get(int(res.stop)), "gap": res.gap}
 
     def iterate(self, k: int) -> None:
         _check(_get_lib().lamp_iterate(self._h, int(k)), self._h)
 
     def objective(self) -> dict:
-        out = (ctypes.c_double * 8)()
+        out = (ctypes.c_double * OBJECTIVE_SLOTS)()
         _check(_get_lib().lamp_objective(self._h, out), self._h)
-        keys = ["cost", "col_res", "row_res", "entropy", "P_eta", "certificate", "dual", "K"]
+        keys = ["cost", "col_res", "row_res", "entropy", "P_eta", "certificate", "dual", "K", "L", "gap"]
         return dict(zip(keys, list(out)))
 
     def dual(self) -> dict:
@@ -418,11 +424,10 @@ def _make_loss_function():
                           eta=eta, **params)
             info = solver.solve()
             obj = solver.objective()
-            loss = obj["cost"] - eta * obj["entropy"]
             ctx.solver = solver
             ctx.info = info
             ctx.obj = obj
-            return torch.tensor(loss, dtype=torch.float64, device=x.device)
+            return torch.tensor(obj["L"], dtype=torch.float64, device=x.device)
 
         @staticmethod
         def backward(ctx, g):

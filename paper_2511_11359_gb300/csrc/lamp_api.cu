@@ -106,7 +106,10 @@ extern "C" int lamp_params_default(lamp_params* p) {
   p->max_iter = 100000;
   p->check_every = 50;
   p->prec = LAMP_PREC_FP32;
+  p->infeas_only = 0;
   p->K = 0.0;
+  p->gap_tol = 0.0;
+  p->gap_every = 0;
   return LAMP_OK;
 }
 
@@ -146,6 +149,10 @@ static int validate(const lamp_problem* pr, const lamp_params* pa, bool device_p
     return fail(nullptr, LAMP_E_INVALID, "LAMP_PREC_BF16_TC applies to LAMP_COST_SQEUCLID and LAMP_COST_COSINE only");
   if (!(pa->K >= 0.0) || !std::isfinite(pa->K)) return fail(nullptr, LAMP_E_INVALID, "K must be >= 0");
   if (pa->tau1 > 0.0 && pa->tau1 * pa->eta > 1.0) return fail(nullptr, LAMP_E_INVALID, "tau1 * eta must be <= 1");
+  if (!(pa->gap_tol >= 0.0) || !std::isfinite(pa->gap_tol))
+    return fail(nullptr, LAMP_E_INVALID, "gap_tol must be >= 0 and finite (0 = no gap test)");
+  if (pa->gap_every < 0) return fail(nullptr, LAMP_E_INVALID, "gap_every must be >= 0 (0 = check_every)");
+  if (pa->infeas_only != 0 && pa->infeas_only != 1) return fail(nullptr, LAMP_E_INVALID, "infeas_only must be 0 or 1");
   (void)device_ptrs;
   return LAMP_OK;
 }
@@ -272,6 +279,7 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
   // the packed sweeps (direct form and tensor cores) derive stream B from stream A
   k.shared_shift = (uses_direct_sweeps(k, params->prec) || params->prec == LAMP_PREC_BF16_TC) ? 1 : 0;
   k.eta = params->eta;
+  k.infeas_only = params->infeas_only;
   k.alpha = params->alpha;
   k.clipb = std::tanh(params->beta / 2.0);
   ctx->log_m = std::log((double)k.m);
@@ -601,7 +609,7 @@ static int run_graph(lamp_ctx* ctx, int slot, int64_t len) {
   return LAMP_OK;
 }
 
-static void fill_result(lamp_ctx* ctx, lamp_result* out) {
+static void fill_result(lamp_ctx* ctx, lamp_result* out, int stop, double gap) {
   if (!out) return;
   const DevState& d = *ctx->host_dev;
   out->iters = d.t;
@@ -610,28 +618,60 @@ static void fill_result(lamp_ctx* ctx, lamp_result* out) {
   out->kappa = d.kappa;
   out->K = ctx->k.K;
   out->status = d.status;
+  out->stop = stop;
+  out->gap = gap;
 }
 
 static int evaluate(lamp_ctx* ctx);
+static int objective_values(lamp_ctx* ctx, double* out);
 
 extern "C" int lamp_solve(lamp_ctx* ctx, lamp_result* out) {
   if (!ctx) return fail(nullptr, LAMP_E_INVALID, "lamp_solve: null context");
-  k_ctrl<<<1, 1, 0, ctx->stream>>>(ctx->w.dev, 0, ctx->params.tol, ctx->params.max_iter, -1, 0);
-  CK(cudaGetLastError());
-  const int64_t L = ctx->params.check_every;
+  const lamp_params& pa = ctx->params;
+  auto arm = [&]() {
+    k_ctrl<<<1, 1, 0, ctx->stream>>>(ctx->w.dev, 0, pa.tol, pa.max_iter, -1, 0);
+    return cudaGetLastError();
+  };
+  CK(arm());
+  const int64_t L = pa.check_every;
+  // primal-dual gap test (App. E.2): every gap_every iterations (a multiple of the polling
+  // interval), one evaluation pass and the dual sweeps on the current X^t
+  const bool use_gap = pa.gap_tol > 0.0;
+  const int64_t gap_every = pa.gap_every > 0 ? pa.gap_every : L;
+  int64_t next_gap = -1;
+  int stop = 0;
+  double gap = NAN;
   for (;;) {
     int rc = run_graph(ctx, 1, L);
     if (rc) return rc;
     if ((rc = poll(ctx))) return rc;
     if (ctx->host_dev->done) break;
+    if (use_gap && ctx->host_dev->t >= next_gap) {
+      double ob[LAMP_OBJECTIVE_SLOTS];
+      if ((rc = objective_values(ctx, ob))) return rc;
+      gap = ob[9];
+      if (gap <= pa.gap_tol) {
+        stop = LAMP_STOP_GAP;
+        break;
+      }
+      next_gap = ctx->host_dev->t + gap_every;
+      CK(arm());  // the evaluation passes leave the device loop stopped
+    }
   }
-  if (ctx->k.shared_shift && ctx->host_dev->status == 0) {
+  const DevState& hd = *ctx->host_dev;
+  if (stop == 0 && hd.status == 0) {
+    // the device's rule (k_col_fin): infeasibility, and for eta > 0 the kappa condition
+    const bool rule = hd.t >= 1 && hd.res <= pa.tol &&
+                      (ctx->k.eta == 0.0 || ctx->k.infeas_only || 1.0 - hd.kappa * ctx->k.eta <= pa.tol);
+    stop = rule ? LAMP_STOP_INFEAS : LAMP_STOP_MAX_ITER;
+  }
+  if (stop != LAMP_STOP_GAP && ctx->k.shared_shift && hd.status == 0) {
     // the regular iterations of the packed direct-form sweeps leave <C, X^t> out: one
     // evaluation pass of the final state provides it
     int rc = evaluate(ctx);
     if (rc) return rc;
   }
-  fill_result(ctx, out);
+  fill_result(ctx, out, stop, gap);
   const DevState& d = *ctx->host_dev;
   if (d.status == LAMP_E_TIMEOUT) {
     if (out) out->status = LAMP_E_TIMEOUT;
@@ -642,7 +682,7 @@ extern "C" int lamp_solve(lamp_ctx* ctx, lamp_result* out) {
     if (out) out->status = LAMP_E_NUMERIC;
     return fail(ctx, LAMP_E_NUMERIC, "non-finite or out-of-range sum at iteration %lld", (long long)d.t);
   }
-  if (!(d.res <= ctx->params.tol)) {
+  if (stop == LAMP_STOP_MAX_ITER) {
     if (out) out->status = LAMP_E_NOT_CONVERGED;
     return fail(ctx, LAMP_E_NOT_CONVERGED, "max_iter reached (t=%lld, infeasibility %.3e)", (long long)d.t, d.res);
   }
@@ -767,8 +807,14 @@ extern "C" int lamp_round(lamp_ctx* ctx, double out[4], double* y, double* delta
   return LAMP_OK;
 }
 
-extern "C" int lamp_objective(lamp_ctx* ctx, double out[8]) {
+extern "C" int lamp_objective(lamp_ctx* ctx, double out[LAMP_OBJECTIVE_SLOTS]) {
   if (!ctx || !out) return fail(ctx, LAMP_E_INVALID, "lamp_objective: null argument");
+  return objective_values(ctx, out);
+}
+
+// the quantities of lamp_objective for the current state (one evaluation pass, then the
+// dual sweeps); leaves the device loop stopped (dev->done set)
+static int objective_values(lamp_ctx* ctx, double* out) {
   int rc = evaluate(ctx);
   if (rc) return rc;
   const DevState& d = *ctx->host_dev;
@@ -782,12 +828,15 @@ extern "C" int lamp_objective(lamp_ctx* ctx, double out[8]) {
   out[4] = d.costA + 2.0 * k.K * d.res - k.eta * H;
   out[5] = (k.eta == 0.0 && d.t >= 1) ? 4.0 * k.K * d.res + 2.0 * k.K * ctx->log_m / (double)d.t : NAN;
   out[7] = k.K;
+  out[8] = d.costA - k.eta * H;  // <C, X^t> - eta H(X^t)  (Eq. prob:primal_eot)
+  out[9] = NAN;
   if (d.status == LAMP_E_TIMEOUT) return fail(ctx, LAMP_E_TIMEOUT, "a device-side wait ran out of its budget");
   if (d.status != 0) return fail(ctx, LAMP_E_NUMERIC, "non-finite or out-of-range sum");
   // the dual bound at theta^t and nu^t (the larger is reported)
   double D2[2];
   if ((rc = dual_values(ctx, D2))) return rc;
   out[6] = std::max(D2[0], D2[1]);
+  out[9] = out[4] - out[6];  // primal-dual gap of the saddle problem (App. E.2 termination)
   return LAMP_OK;
 }
 

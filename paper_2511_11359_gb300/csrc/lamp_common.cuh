@@ -81,6 +81,8 @@ struct Consts {
   // point-cloud ground cost of the direct form: 0 |x - y|^2, 1 sum_k |x_k - y_k| (l1),
   // 2 max_k |x_k - y_k| (l-inf)
   int32_t cost_op = 0;
+  // eta > 0: 1 = the termination rule uses the infeasibility alone (no kappa condition)
+  int32_t infeas_only = 0;
 };
 
 // Parameters of one iteration's sweeps, derived from kappa_t alone.
@@ -381,6 +383,10 @@ cudaError_t launch_check_marginals(const Inputs& in, const Consts& k, const Work
 cudaError_t launch_init_state(const Inputs& in, const Consts& k, const Work& w, int zero, cudaStream_t st);
 cudaError_t launch_prime(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
                          cudaStream_t st);
+// after launch_prime: per row and split, max_j (v_ij - Br_j) with the primed row shifts
+// applied (Work::rowmax, stream A slot); the column data's second field holds Br_j
+cudaError_t launch_rowmax_refined(const Inputs& in, const Consts& k, const Work& w, const Geometry& g,
+                                  cudaStream_t st);
 // eval = 1: an evaluation pass, whose column sweep also accumulates <C, X^t> (the
 // packed direct-form column sweep leaves it out of the regular iterations)
 cudaError_t launch_iteration(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,

@@ -228,10 +228,18 @@ k_dual_cols(const Work w, int cur, int which, const double* __restrict__ c, floa
     const double phi = which ? w.nu[cur][j] : w.theta[cur][j];
     const SweepParams sp = make_sweep_params(k.kap_ovr, k);
     const double sny = k.zdot ? k.s * w.ny[j] : 0.0;
-    float dB;
-    const float4 cd = column_data(phi, phi, sny, sp, k, &dB);
-    colq_s[j] = cd;
-    if (colq2_s) store_pair_entry(colq2_s, j, cd.x, cd.y, dB, cd.w);
+    if (k.eta > 0.0) {
+      float dB;
+      const float4 cd = column_data(phi, phi, sny, sp, k, &dB);
+      colq_s[j] = cd;
+      if (colq2_s) store_pair_entry(colq2_s, j, cd.x, cd.y, dB, cd.w);
+    } else {
+      // eta = 0: the row-max passes read {Bq_j, Br_j} (the offset on the grid and the
+      // remainder Br_j = Bcol_j - Bq_j, |Br_j| <= g/2, as a float) instead of a weight
+      const double b = sp.lamA * (sny + 2.0 * k.K * phi);
+      const double q = quantize(b, sp.g);
+      colq_s[j] = make_float4((float)q, (float)(b - q), (float)q, (float)(b - q));
+    }
     v = c[j] * phi;
   }
   v = block_sum(v, sh);
@@ -251,10 +259,11 @@ k_dual_rows(const Work w, const float2* __restrict__ rs_s, int splits, const dou
     const double snx = k.zdot ? k.s * w.nx[i] : 0.0;
     double mn;
     if (!soft) {
-      // max_j (a z_ij - Bq_j) = -lambda (min_j (C_ij + 2K phi_j) - s|x_i|^2 [dot form])
+      // refinement pass: M = max_j (a z_ij - Bq_j - Br_j - Rq_i)
+      //                    = -lambda (min_j (C_ij + 2K phi_j) - s|x_i|^2 [dot form]) - Rq_i
       float M = -INFINITY;
       for (int s = 0; s < splits; ++s) M = fmaxf(M, w.rowmax[((int64_t)s * 2 + 0) * k.n + i]);
-      mn = -(double)M / sp.lamA + snx;
+      mn = -((double)rs_s[i].x + (double)M) / sp.lamA + snx;
     } else {
       // softmin = -(1/kappa) log Z_i, log2 Z_i = Rq_i - lambda s|x_i|^2 + log2 S_i
       double S = 0.0;
@@ -326,8 +335,9 @@ cudaError_t launch_dual(const Inputs& in, const Consts& k, const Work& w, const 
   double* res = colp + cb;
   Consts k2 = k;
   k2.same_kappa = 1;
-  // eta > 0: the softmin at kappa = 1/eta; eta = 0: the row min, from row maxima at a
-  // kappa large enough that the offset grid is fine relative to lambda (see the header)
+  // eta > 0: the softmin at kappa = 1/eta; eta = 0: the row min, from two row-max passes
+  // at a large kappa (the second with the row shifts of the first and the column
+  // remainders subtracted)
   const bool soft = k.eta > 0.0;
   k2.kap_ovr = soft ? 1.0 / k.eta : 65536.0 / k.K;
   Work w2 = w;
@@ -341,6 +351,13 @@ cudaError_t launch_dual(const Inputs& in, const Consts& k, const Work& w, const 
   if (e != cudaSuccess) return e;
   if (soft) {
     e = launch_iteration_part(in, k2, w2, g, prec, 0, 0, st);
+    if (e != cudaSuccess) return e;
+  } else {
+    // second pass with the primed row shifts: near each row's maximum |u| is a few grid
+    // steps, so its float32 rounding (and that of the remainder) is ~2^-24 g, and the row
+    // minimum min_j (C_ij + 2K phi_j) of the kernels' cost comes out with an absolute error
+    // of order 2^-46 W instead of W 2^-24 (W the offset bound, a few K)
+    e = launch_rowmax_refined(in, k2, w2, g, st);
     if (e != cudaSuccess) return e;
   }
   k_dual_rows<<<(unsigned)rb, kT, 0, st>>>(w, w.rowshift[nx], g.rows_split, in.r, soft ? 1 : 0, rowp, k2);

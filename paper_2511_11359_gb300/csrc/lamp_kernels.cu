@@ -76,7 +76,10 @@ __device__ __forceinline__ void stage_points(float* __restrict__ s, const float*
 constexpr int kPT = 128;
 constexpr int kThreads = 256;
 
-enum SweepMode : int { M_ROWSUM = 0, M_COLSUM = 1, M_MAX = 2, M_KMAX = 3, M_GRAD = 4 };
+// M_MAX2: row maxima of u_ij = v_ij - Br_j with the row shifts applied and the column
+// remainders Br_j (floats, in the column data's second field) subtracted: the refinement
+// pass of the eta = 0 dual bound (see launch_dual), accurate to a few ulps of the grid
+enum SweepMode : int { M_ROWSUM = 0, M_COLSUM = 1, M_MAX = 2, M_KMAX = 3, M_GRAD = 4, M_MAX2 = 5 };
 
 // buffers of a sweep, indexed by the state-buffer parity dev->cur
 struct SweepIO {
@@ -133,6 +136,9 @@ k_pts_sweep(const float* __restrict__ P_out, const float* __restrict__ P_in, int
       oB[a] = 0.f;
     } else if (MODE == M_MAX) {
       oA[a] = 0.f;
+      oB[a] = 0.f;
+    } else if (MODE == M_MAX2) {
+      oA[a] = off2[go].x;
       oB[a] = 0.f;
     } else {
       float2 q = off2[go];
@@ -260,6 +266,17 @@ k_pts_sweep(const float* __restrict__ P_out, const float* __restrict__ P_in, int
           mx[a][0] = fmaxf(mx[a][0], __fmaf_rn(ahA, z[a][b], -dat[b].x));
           mx[a][1] = fmaxf(mx[a][1], __fmaf_rn(ahB, z[a][b], -dat[b].z));
         }
+    } else if (MODE == M_MAX2) {
+      // u = a z - (Rq + Bq) - Br: the offsets' sum is exact on the grid, a z exact in the fma,
+      // and |u| is a few grid steps near the row maximum (Rq comes from the M_MAX pass)
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          const float zz = z[a][b];
+          const float u = __fmaf_rn(alA, zz, __fmaf_rn(ahA, zz, -(oA[a] + dat[b].x))) - dat[b].y;
+          mx[a][0] = fmaxf(mx[a][0], u);
+        }
     } else if (MODE == M_KMAX) {
       // unscaled squared distance |x|^2 + |y|^2 - 2 x.y in float32; oA holds |x_o|^2
 #pragma unroll
@@ -307,7 +324,7 @@ k_pts_sweep(const float* __restrict__ P_out, const float* __restrict__ P_in, int
         if (tx == 0 && go < n_out) part[((int64_t)split * NACC + q) * n_out + go] = v;
       }
     }
-  } else if (MODE == M_MAX || MODE == M_KMAX) {
+  } else if (MODE == M_MAX || MODE == M_KMAX || MODE == M_MAX2) {
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
       int64_t go = o0 + ((a < 4) ? (ty * 4 + a) : (64 + ty * 4 + a - 4));
@@ -340,7 +357,7 @@ k_pts_sweep(const float* __restrict__ P_out, const float* __restrict__ P_in, int
 constexpr int kDR = 8;        // rows per CTA in the row sweep
 constexpr int kDChunk = 1024; // columns per CTA step (4 per thread, stride 256)
 
-template <int MODE>  // M_ROWSUM or M_MAX
+template <int MODE>  // M_ROWSUM, M_MAX or M_MAX2
 __global__ void __launch_bounds__(kThreads)
 k_dense_rows(const float* __restrict__ C, int64_t ldc, int64_t n, int64_t m, const Work w,
              int chunks_per_split, const Consts k) {
@@ -408,6 +425,13 @@ k_dense_rows(const float* __restrict__ C, int64_t ldc, int64_t n, int64_t m, con
         }
         ff_add(hiA[a], loA[a], sA);
         ff_add(hiB[a], loB[a], sB);
+      } else if (MODE == M_MAX2) {
+        // refinement pass of the eta = 0 dual bound (see k_pts_sweep, M_MAX2)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float zz = cv[a][q];
+          mA[a] = fmaxf(mA[a], __fmaf_rn(alA, zz, __fmaf_rn(ahA, zz, -(oA[a] + cd[q].x))) - cd[q].y);
+        }
       } else {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -854,7 +878,8 @@ k_col_fin(const Work w, int splits, const double* __restrict__ cvec, int rowbloc
       dev->done = 1;
     } else if (eval_only) {
       dev->done = 1;
-    } else if ((dev->t >= 1 && R <= dev->tol && (k.eta == 0.0 || 1.0 - dev->kappa * k.eta <= dev->tol)) ||
+    } else if ((dev->t >= 1 && R <= dev->tol &&
+                (k.eta == 0.0 || k.infeas_only || 1.0 - dev->kappa * k.eta <= dev->tol)) ||
                dev->t >= dev->tmax) {
       dev->done = 1;
     } else {
@@ -986,6 +1011,8 @@ static cudaError_t launch_row_sweep(const Inputs& in, const Consts& k, const Wor
     dim3 grid((unsigned)cdiv(k.n, kDR), (unsigned)g.rows_split);
     if (mode == M_ROWSUM)
       k_dense_rows<M_ROWSUM><<<grid, kThreads, 0, st>>>(in.C, in.ldc, k.n, k.m, w, cps, k);
+    else if (mode == M_MAX2)
+      k_dense_rows<M_MAX2><<<grid, kThreads, 0, st>>>(in.C, in.ldc, k.n, k.m, w, cps, k);
     else
       k_dense_rows<M_MAX><<<grid, kThreads, 0, st>>>(in.C, in.ldc, k.n, k.m, w, cps, k);
     return cudaGetLastError();
@@ -999,6 +1026,8 @@ static cudaError_t launch_row_sweep(const Inputs& in, const Consts& k, const Wor
   }
   if (mode == M_ROWSUM)
     return launch_pts<M_ROWSUM, 0>(in.x, in.y, k.n, k.m, k.d, io, w.rowpart, nullptr, g.rows_split, w.dev, k, st);
+  if (mode == M_MAX2)
+    return launch_pts<M_MAX2, 0>(in.x, in.y, k.n, k.m, k.d, io, nullptr, w.rowmax, g.rows_split, w.dev, k, st);
   return launch_pts<M_MAX, 0>(in.x, in.y, k.n, k.m, k.d, io, nullptr, w.rowmax, g.rows_split, w.dev, k, st);
 }
 
@@ -1030,6 +1059,11 @@ cudaError_t launch_prime(const Inputs& in, const Consts& k, const Work& w, const
   if (e != cudaSuccess) return e;
   k_prime_fin<<<(unsigned)cdiv(k.n, 256), 256, 0, st>>>(w, g.rows_split, k);
   return cudaGetLastError();
+}
+
+cudaError_t launch_rowmax_refined(const Inputs& in, const Consts& k, const Work& w, const Geometry& g,
+                                  cudaStream_t st) {
+  return launch_row_sweep(in, k, w, g, M_MAX2, st);
 }
 
 cudaError_t launch_iteration_part(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
@@ -1079,6 +1113,7 @@ void prepare_kernels() {
   set_attr<M_ROWSUM, 0>();
   set_attr<M_COLSUM, 0>();
   set_attr<M_MAX, 0>();
+  set_attr<M_MAX2, 0>();
   set_attr<M_KMAX, 0>();
   set_attr<M_GRAD, 1>();
   set_attr<M_GRAD, 2>();

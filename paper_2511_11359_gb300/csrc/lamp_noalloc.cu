@@ -15,8 +15,12 @@
 // library holds its kScratchBytes until the process exits.  Host code cannot
 // use the variable's name as a device pointer (in host code it names a host
 // shadow), so the first call on each device, with that device current, looks
-// up the real address with cudaGetSymbolAddress and caches it per device.
-// Make that first call on a device before any stream capture is started.
+// up the real address with cudaGetSymbolAddress and caches it per device,
+// together with the device's current CUDA context.  A call that finds another
+// context current on that device (the primary context was reset or torn down
+// and re-created, which reloads the module and can move the array) looks the
+// address up again.  Make the first call on a device, and the first call after
+// such a reset, before any stream capture is started.
 //
 // All calls on a device share the one array and leave their contents in it;
 // the call clears what must start at zero.  Calls whose GPU work overlaps
@@ -37,7 +41,24 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 void* g_scratch_addr[kMaxDevices] = {};
+void* g_scratch_ctx[kMaxDevices] = {};  // the context the cached address belongs to
 std::mutex g_scratch_mu;
+
+// the calling thread's current CUDA context (driver API, looked up once through the
+// runtime's entry-point query so that the library needs no link to libcuda)
+cudaError_t current_context(void** out) {
+  typedef int (*CtxGetCurrentFn)(void**);
+  static CtxGetCurrentFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) return cudaErrorNotSupported;
+    fn = reinterpret_cast<CtxGetCurrentFn>(p);
+  }
+  *out = nullptr;
+  return fn(out) == 0 ? cudaSuccess : cudaErrorIncompatibleDriverContext;
+}
 
 int noalloc_fail(int code, const char* msg) {
   lamp::set_last_error_null(msg);
@@ -115,15 +136,22 @@ extern "C" int lamp_marginals_noalloc(const lamp_problem* prob, double K, double
   void* base = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_addr[devi]) {
+    // the runtime makes the device's primary context current on first use; the symbol
+    // lookup below does that too, so query the context after it when nothing is cached
+    void* ctx = nullptr;
+    cudaError_t e = current_context(&ctx);
+    if (e != cudaSuccess) return noalloc_fail(LAMP_E_CUDA, "cuCtxGetCurrent failed");
+    if (!g_scratch_addr[devi] || !ctx || ctx != g_scratch_ctx[devi]) {
       void* p = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess || !p) {
         char msg[160];
         std::snprintf(msg, sizeof(msg), "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
         return noalloc_fail(LAMP_E_CUDA, msg);
       }
+      if (current_context(&ctx) != cudaSuccess || !ctx) return noalloc_fail(LAMP_E_CUDA, "cuCtxGetCurrent failed");
       g_scratch_addr[devi] = p;
+      g_scratch_ctx[devi] = ctx;
     }
     base = g_scratch_addr[devi];
   }

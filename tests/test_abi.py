@@ -40,6 +40,7 @@ def test_params_default(L):
     p = L.default_params()
     assert (p.eta, p.tau1, p.tau2, p.alpha, p.beta, p.tol) == (0.0, 0.0, 0.0, 0.01, 1.1, 1e-6)
     assert p.max_iter == 100000 and p.check_every == 50 and p.prec == L.PREC_FP32 and p.K == 0.0
+    assert p.gap_tol == 0.0 and p.gap_every == 0 and p.infeas_only == 0
 
 
 def _prob(L, **kw):
@@ -63,6 +64,9 @@ BAD = [
     ({"kind": 2}, {"prec": 1}), ({"kind": 3}, {"prec": 1}), ({"kind": 0, "C": 0x10, "ldc": 9}, {"prec": 1}),
     ({"n": 1 << 32}, {}), ({"m": (1 << 31) + 1}, {}), ({}, {"check_every": 100001}),
     ({"cost_scale": float("inf")}, {}), ({}, {"alpha": float("nan")}), ({}, {"K": float("inf")}),
+    # primal-dual gap termination and the eta > 0 rule switch
+    ({}, {"gap_tol": -1e-9}), ({}, {"gap_tol": float("nan")}), ({}, {"gap_tol": float("inf")}),
+    ({}, {"gap_every": -1}), ({}, {"infeas_only": 2}),
 ]
 
 
@@ -86,6 +90,13 @@ def test_null_context_calls(L):
     out = ctypes.c_void_p()
     assert L.lib.lamp_create(ctypes.byref(out), None, None, None) == L.LAMP_E_INVALID
     assert L.lib.lamp_create(None, None, None, None) == L.LAMP_E_INVALID
+
+
+def test_objective_slots_match_header(L):
+    src = (ROOT / "include" / "lamp.h").read_text()
+    assert int(re.search(r"#define LAMP_OBJECTIVE_SLOTS (\d+)", src).group(1)) == L.OBJECTIVE_SLOTS
+    out = (ctypes.c_double * L.OBJECTIVE_SLOTS)()
+    assert L.lib.lamp_objective(None, out) == L.LAMP_E_INVALID
 
 
 def test_evaluation_entry_points_validate_on_host(L):

@@ -63,6 +63,19 @@ def _dot_slack(w, s):
     return w.d * 2.0 ** -24 * s * (nx + ny)
 
 
+def _cost_err(w, s):
+    """Bound on max_ij |C~_ij - C_ij| of the kernels' float32 cost: 0 for a stored cost,
+    the float32 evaluation of the squared differences (direct form, d <= 8), the dot-form
+    bound otherwise."""
+    if w.kind == "dense":
+        return 0.0
+    if w.d > 8:
+        return _dot_slack(w, s)
+    from tests.gpu_util import cost_error
+
+    return cost_error(w)
+
+
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_round_matches_oracle(case):
     w, C, s, K, st, sol = _setup(case)
@@ -98,13 +111,47 @@ def test_dual_matches_oracle(case):
     D = sol.dual()
     ref_t = O.saddle_dual(C, w.r, w.c, K, st.theta, eta)
     ref_n = O.saddle_dual(C, w.r, w.c, K, st.nu, eta)
-    # eta = 0: the row minimum from float32 row maxima with offsets on the kernels' grid
-    # (|error| about 1e-6 K); eta > 0: the row sums at kappa = 1/eta
-    tol = 2e-6 * K + 4 * _dot_slack(w, s)
-    assert abs(D["theta"] - ref_t) <= tol, (D["theta"], ref_t)
-    assert abs(D["nu"] - ref_n) <= tol, (D["nu"], ref_n)
+    # D is 1-Lipschitz in the cost (max norm): the kernels' float32 cost differs from the
+    # oracle's by at most the cost error bound; beyond it, eta = 0 is exact to ~1e-12 K
+    # (two row-max passes) and eta > 0 carries the ex2 error, ~2^-22 eta
+    tol = 1e-9 * K + 2.0 * _cost_err(w, s) + (4e-7 * eta if eta > 0 else 0.0)
+    assert abs(D["theta"] - ref_t) <= tol, (D["theta"], ref_t, tol)
+    assert abs(D["nu"] - ref_n) <= tol, (D["nu"], ref_n, tol)
     obj = sol.objective()
     assert obj["dual"] == max(D["theta"], D["nu"])
+    assert obj["gap"] == pytest.approx(obj["P_eta"] - obj["dual"], rel=0, abs=1e-12 * K)
+    sol.close()
+
+
+EXACT_CASES = [
+    # points on a 1/16 grid: every squared distance (direct form) and every x.y (dot form,
+    # bf16 tensor cores included) is exact in float32, so the kernels' cost is the oracle's
+    ("dy3", 300, 257, 3, "fp32"),
+    ("dy16", 400, 300, 16, "fp32"),
+    ("dy64tc", 384, 300, 64, "bf16_tc"),
+    ("dense_exact", 290, 1100, 0, "fp32"),
+]
+
+
+@pytest.mark.parametrize("case", EXACT_CASES, ids=[c[0] for c in EXACT_CASES])
+def test_dual_is_exact_on_an_exact_cost(case):
+    """eta = 0 dual D(phi) (Eq. def:dual_spp) on costs the float32 kernels represent exactly:
+    |D_gpu - D_oracle| <= 1e-9 K at theta^T and nu^T."""
+    name, n, m, d, prec = case
+    seed = sum(name.encode()) % 991
+    if d == 0:
+        w = W.dense_problem(name, n, m, seed=seed)
+    else:
+        dist = "gauss_shift" if d > 8 else "uniform"
+        w = W.points_problem(name, n, m, d, seed=seed, dist=dist, marg="random", cost_scale=1.0, grid_step=16)
+    C, s, K = oracle_cost(w)
+    st = O.lamp_run(C, w.r, w.c, O.LampParams(K=K), 60)
+    sol, _, _ = gpu_solver(w, K=K, scale=s, prec=prec, check_every=5)
+    sol.set_state(st.nu, st.theta, st.kappa, st.t)
+    D = sol.dual()
+    for key, phi in (("theta", st.theta), ("nu", st.nu)):
+        ref = O.saddle_dual(C, w.r, w.c, K, phi, 0.0)
+        assert abs(D[key] - ref) <= 1e-9 * K, (name, key, D[key] - ref)
     sol.close()
 
 
@@ -121,7 +168,7 @@ def test_round_dual_and_certificate_bracket_the_lp_optimum():
         obj = sol.objective()
         rd = sol.round()
         D = sol.dual()
-        assert max(D["theta"], D["nu"]) <= ot + 2e-6 * K
+        assert max(D["theta"], D["nu"]) <= ot + 1e-9 * K + 2.0 * _cost_err(w, s)
         assert rd["cost"] >= ot - OBJ_TOL * ot
         assert rd["cost"] - ot <= obj["certificate"] + OBJ_TOL * ot
         assert obj["certificate"] == pytest.approx(4 * K * obj["col_res"] + 2 * K * math.log(w.m) / T, rel=1e-12)
@@ -179,3 +226,38 @@ def test_apply_map_matches_oracle(case, kv):
     colX = (w.r[:, None] * p).sum(axis=0)
     assert np.abs(colr - colX).max() <= rel * colX.max()
     sol.close()
+
+
+@pytest.mark.parametrize("eta", [0.0, 0.05])
+def test_solve_stops_on_the_primal_dual_gap(eta):
+    """gap_tol > 0: lamp_solve stops at the first evaluated X^t whose primal-dual gap
+    P^eta(X^t) - max D (App. B duals, App. E.2 termination) is <= gap_tol, with the
+    infeasibility rule off (tol = 0).  The gap then certifies the optimum: by weak duality
+    and Lemma l1_prob_equiv, D <= OT* (EOT*) <= P^eta, checked against the LP (eta = 0) and
+    FP64 Sinkhorn (eta > 0) on a cost the kernels represent exactly (points on a 1/16 grid).
+    The float32 primal is known to ~1e-7 K, so the tolerance is 1e-6 K, not the 1e-10 of the
+    paper's FP64 runs."""
+    w = W.points_problem("gap", 40, 36, 2, seed=5, dist="uniform", marg="random", cost_scale=1.0, eta=eta,
+                         grid_step=16)
+    C, s, K = oracle_cost(w)
+    if eta == 0.0:
+        ref = O.ot_lp(C, w.r, w.c)
+    else:
+        ref = O.eot_value(C, O.sinkhorn_log(C, w.r, w.c, eta, tol=1e-14)[0], eta)
+    gap_tol = 1e-6 * K
+    sol, _, _ = gpu_solver(w, K=K, scale=s, eta=eta, tol=0.0, max_iter=400000, check_every=100,
+                           gap_tol=gap_tol, gap_every=500)
+    res = sol.solve(allow_not_converged=False)
+    assert res["stop"] == "gap" and res["gap"] <= gap_tol, res
+    obj = sol.objective()  # the same state: the same gap
+    assert obj["gap"] == pytest.approx(res["gap"], rel=0, abs=1e-12 * K)
+    assert obj["dual"] <= ref + 1e-9 * K, (obj["dual"], ref)
+    assert ref <= obj["P_eta"] + 2e-7 * K, (obj["P_eta"], ref)
+    assert obj["P_eta"] - ref <= gap_tol + 1e-9 * K
+    sol.close()
+    # gap_tol = 0 keeps the infeasibility rule alone
+    sol2, _, _ = gpu_solver(w, K=K, scale=s, eta=eta, tol=1e-5, max_iter=400000, check_every=10,
+                            infeas_only=1)
+    r2 = sol2.solve(allow_not_converged=False)
+    assert r2["stop"] == "infeasibility" and r2["infeas"] <= 1e-5 and np.isnan(r2["gap"])
+    sol2.close()

@@ -69,6 +69,15 @@ MUTANTS = [
      DT.test_dt_summand_matches_independent_form, (6, 6, 0.05, 3)),
     ("Dt_summand", "- D_Ha(info.thetabar, prev.theta, calpha)", "+ D_Ha(info.thetabar, prev.theta, calpha)",
      DT.test_dt_summand_matches_independent_form, (5, 4, 0.0, 1)),
+    ("penalized_objective", "2.0 * K * np.abs", "K * np.abs",
+     PINS.test_penalty_coefficient_is_exact_where_half_of_it_is_not, ()),
+    ("penalized_objective", "2.0 * K * np.abs", "0.0 * K * np.abs", PINS.test_penalized_objective_exact_penalty, (0.0,)),
+    ("penalized_objective", "- eta * entropy(X)", "+ eta * entropy(X)", PINS.test_penalized_objective_exact_penalty,
+     (0.05,)),
+    ("penalized_objective", "X.sum(axis=0) - c", "X.sum(axis=1)[: c.shape[0]] - c",
+     PINS.test_penalized_objective_exact_penalty, (0.0,)),
+    ("objective_report", '"P_eta": penalized_objective(X, C, c, K, eta)', '"P_eta": cost + K * col_res - eta * H',
+     PINS.test_objective_report_uses_the_pinned_penalty, ()),
     ("eot_value", "- eta * entropy(X)", "+ eta * entropy(X)",
      GOLD.test_sinkhorn_plan_and_value_equal_closed_form, (GOLD.FIX["entropic"][0],)),
     ("entropy", "np.log(Xp)", "np.log2(Xp)",

@@ -489,3 +489,150 @@ def test_point_costs_match_scipy_distances():
     u = x / np.linalg.norm(x, axis=1, keepdims=True)
     v = y / np.linalg.norm(y, axis=1, keepdims=True)
     np.testing.assert_allclose(O.cosine_cost(x, y), 0.5 * O.sqeuclid_cost(u, v), rtol=1e-12, atol=1e-13)
+
+
+# ----------------------------------------------------------------------------- exact penalty
+
+
+def _lp_plan(C, r, c):
+    """An optimal plan of Eq. prob:primal_ot from HiGHS (for the equality check below)."""
+    from scipy.optimize import linprog
+    from scipy.sparse import coo_matrix, vstack
+
+    n, m = C.shape
+    idx = np.arange(n * m)
+    A = vstack([coo_matrix((np.ones(n * m), (idx // m, idx)), shape=(n, n * m)),
+                coo_matrix((np.ones(n * m), (idx % m, idx)), shape=(m, n * m))]).tocsr()
+    res = linprog(C.ravel(), A_eq=A, b_eq=np.concatenate([r, c]), bounds=(0, None), method="highs",
+                  options={"primal_feasibility_tolerance": 1e-10, "dual_feasibility_tolerance": 1e-10})
+    return res.x.reshape(n, m)
+
+
+def _row_feasible_family(C, r, Xstar, rng):
+    """Row-feasible plans diag(r) p, p row-stochastic: Dirichlet rows, the greedy plan that
+    puts each row's mass on its cheapest column (cost below OT*, large column residual),
+    and blends of the greedy plan and of random plans with the optimum."""
+    n, m = C.shape
+    greedy = np.zeros((n, m))
+    greedy[np.arange(n), C.argmin(axis=1)] = r
+    fam = [greedy]
+    for a in (0.05, 0.2, 0.5, 0.9):
+        fam.append((1 - a) * Xstar + a * greedy)
+    for conc in (0.05, 1.0, 20.0):
+        p = rng.dirichlet(np.full(m, conc), size=n)
+        fam.append(r[:, None] * p)
+        fam.append(0.7 * Xstar + 0.3 * r[:, None] * p)
+    return fam
+
+
+@pytest.mark.parametrize("eta", [0.0, 0.05])
+def test_penalized_objective_exact_penalty(eta):
+    """Lemma l1_prob_equiv (App. C): with the penalty coefficient 2||C||_inf the penalised
+    problem (Eq. prob:l1_ot_primal) over row-stochastic p has the same optimal value as OT
+    (eta = 0, part a) and, for eta <= K / log(max_j 1/c_j), as EOT (part b): P^eta(X) is
+    >= that value for every row-feasible X and equal to it at the optimal plan (LP plan /
+    Sinkhorn plan).  A smaller coefficient lets the greedy plan (every row on its cheapest
+    column) fall below the optimum."""
+    n, m = 9, 11
+    C, r, c = small_points(n, m, seed=17, scale=1.0)
+    K = O.sup_norm(C)
+    rng = np.random.default_rng(5)
+    if eta == 0.0:
+        vstar = O.ot_lp(C, r, c)
+        Xstar = _lp_plan(C, r, c)
+    else:
+        assert eta <= K / math.log(1.0 / c.min())
+        Xstar, f, g, _ = O.sinkhorn_log(C, r, c, eta, tol=1e-14)
+        vstar = O.eot_value(C, Xstar, eta)
+    assert abs(O.penalized_objective(Xstar, C, c, K, eta) - vstar) <= 1e-9
+    vals = [O.penalized_objective(X, C, c, K, eta) for X in _row_feasible_family(C, r, Xstar, rng)]
+    assert min(vals) >= vstar - 1e-10, (min(vals), vstar)
+    # without the penalty the greedy plan is below the optimum: the penalty is what lifts it
+    assert O.eot_value(C, _row_feasible_family(C, r, Xstar, rng)[0], eta) < vstar
+
+
+def test_penalty_coefficient_is_exact_where_half_of_it_is_not():
+    """The factor 2 of the penalty 2||C||_inf ||col - c||_1 (Eq. prob:l1_ot_primal).  The proof
+    of Lemma l1_prob_equiv (b) makes the penalised and the EOT problem share their minimiser
+    whenever the penalty coefficient mu is at least ||psi*||_inf for an optimal column
+    multiplier psi* (Lemma affine_minimizer); psi* is fixed up to a constant (sum col = sum c),
+    so the smallest such norm is half the range of Sinkhorn's column potentials g.  On a
+    problem with a tiny c_j and eta = 0.2 K that range lies between 2K and 4K: mu = 2K is
+    exact (P^eta >= EOT* on every row-feasible X, = at the optimum), while mu = K is not:
+    moving mass delta within a row from the column of max g to the column of min g changes
+    the entropic cost by delta (min g - max g) and the penalty by 2 mu delta, a net decrease."""
+    w = W.points_problem("t", 8, 9, 2, 17, dist="uniform", marg="random", cost_scale=1.0)
+    C = O.cost_matrix(w)
+    C = C / C.max()
+    K = O.sup_norm(C)
+    r = w.r
+    c = w.c.copy()
+    c[0] = 1e-7
+    c /= c.sum()
+    eta = 0.2 * K
+    Xs, f, g, _ = O.sinkhorn_log(C, r, c, eta, tol=1e-14)
+    spread = g.max() - g.min()
+    assert 2.2 * K < spread < 3.8 * K, spread
+    vstar = O.eot_value(C, Xs, eta)
+    assert abs(O.penalized_objective(Xs, C, c, K, eta) - vstar) <= 1e-12
+    jhi, jlo = int(g.argmax()), int(g.argmin())
+    fam = []
+    for i in range(C.shape[0]):
+        for frac in (1e-3, 1e-2, 1e-1):
+            X = Xs.copy()
+            dlt = frac * X[i, jlo]  # small against the receiving entry (c_jlo is tiny)
+            X[i, jhi] -= dlt
+            X[i, jlo] += dlt
+            fam.append(X)
+    fam += _row_feasible_family(C, r, Xs, np.random.default_rng(8))
+    vals = np.array([O.penalized_objective(X, C, c, K, eta) for X in fam])
+    assert vals.min() >= vstar - 1e-12, vals.min() - vstar
+    # the same moves with half the coefficient go below the optimum
+    half = [O.eot_value(C, X, eta) + K * np.abs(X.sum(0) - c).sum() for X in fam[:2]]
+    assert max(half) < vstar
+
+
+def test_objective_report_uses_the_pinned_penalty():
+    """objective_report's P^eta and L are the pinned functions of X^t."""
+    C, r, c = small_points(7, 8, seed=3)
+    K = O.sup_norm(C)
+    st = O.lamp_run(C, r, c, O.LampParams(eta=0.02), 40)
+    rep = O.objective_report(C, r, c, K, 0.02, st)
+    X = rep["X"]
+    assert rep["P_eta"] == O.penalized_objective(X, C, c, K, 0.02)
+    assert rep["L"] == O.eot_value(C, X, 0.02)
+
+
+def test_certificate_terms_of_the_proof():
+    """Prop. infeas_bound (a) is the sum of two bounds from its proof (Lemma last_iterate,
+    App. D), each checked on its own along a trajectory at every t >= 1:
+      Round term  <C, Round(X^t)> - <C, X^t> <= K ||Round(X^t) - X^t||_1 <= 2K res_t
+                  (Hoelder, Lemma jason_rounding);
+      LAMP term   <C, X^t> - OT* <= -2K <nu^t, col(X^t) - c> + 2K log m / t
+                  <= 2K res_t + 2K log m / t.
+    certificate_rhs adds the right sides: 4K res_t + 2K log m / t.  The inequality pins the
+    constant from below only (a larger constant would still bound the gap)."""
+    n, m = 10, 12
+    C, r, c = small_points(n, m, seed=29, scale=1.3)
+    K = O.sup_norm(C)
+    ot = O.ot_lp(C, r, c)
+    seen = []
+
+    def rec(s, info):
+        if s.t == 0:
+            return
+        X = r[:, None] * O.dual_to_primal(C, K, s.kappa, s.nu)[0]
+        col = X.sum(0)
+        res = float(np.abs(col - c).sum())
+        Xr = O.round_plan(X, r, c)
+        cx, crx = float((C * X).sum()), float((C * Xr).sum())
+        assert crx - cx <= K * np.abs(Xr - X).sum() + 1e-12
+        assert np.abs(Xr - X).sum() <= 2 * res + 1e-12
+        lamp_term = -2 * K * float(s.nu @ (col - c)) + 2 * K * math.log(m) / s.t
+        assert cx - ot <= lamp_term + 1e-12
+        assert lamp_term <= 2 * K * res + 2 * K * math.log(m) / s.t + 1e-12
+        seen.append((crx - ot, O.certificate_rhs(K, res, m, s.t), 2 * K * res + lamp_term))
+        assert crx - ot <= 2 * K * res + lamp_term + 1e-12 <= O.certificate_rhs(K, res, m, s.t) + 2e-12
+
+    O.lamp_run(C, r, c, O.LampParams(), 1500, record=rec)
+    assert len(seen) == 1499

@@ -1,6 +1,7 @@
 """lamp_marginals_noalloc, the entry point for callers that may not allocate device
 memory, against the regular context path (lamp_set_state + lamp_objective +
-lamp_get_state) on the same state, through the C ABI, on two calls in a row.
+lamp_get_state) on the same state, through the C ABI, on two calls in a row, and
+against the FP64 oracle's marginals of the same (nu, kappa).
 
 Collected last on purpose: if it fails, a run that stops at the first failure has
 already run every other test."""
@@ -73,6 +74,12 @@ def test_noalloc_matches_context_path_on_two_calls(kind):
         assert abs(cost.item() - obj["cost"]) <= OBJ_TOL * abs(obj["cost"])
         assert abs(np.abs(cl - w.c).sum() - obj["col_res"]) <= 1e-6 * obj["col_res"] + RES_FLOOR
         assert abs(cl.sum() - 1.0) <= 1e-6
+        # the FP64 oracle on the same (nu, kappa): col(X) and log Z of X = diag(r) p^{1/kappa}(nu)
+        ocol, olz = O.marginals_from_state(C, w.r, K, st["kappa"], st["nu"])
+        assert_logZ_close(lz, olz, LOGZ_TOL, what=f"noalloc log Z vs oracle, T={T}")
+        assert np.abs(cl - ocol).sum() <= 1e-6  # col(X) sums to 1: 1e-6 relative in the L1 norm
+        ocost = float((C * (w.r[:, None] * O.dual_to_primal(C, K, st["kappa"], st["nu"])[0])).sum())
+        assert abs(cost.item() - ocost) <= OBJ_TOL * abs(ocost)
     s.close()
 
 
