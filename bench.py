@@ -228,6 +228,68 @@ def time_oracle(w, seconds: float, max_points: int, min_iters: int = 2, fixed_it
     return ns * ms * it / el, it, el, desc
 
 
+GOLDEN_STATES = os.path.join(ROOT, "tests", "golden", "highdim4096_states.npz")
+
+
+def precision_report(L, torch, devc):
+    """Error of the BF16 tensor-core path and of the plain FP32 path against the FP64
+    oracle on the unrounded problem, on a 4096 x 4096 sample of the highdim workload
+    (the first 4096 source and target points, uniform marginals).  The oracle's states
+    come from tests/golden/highdim4096_states.npz (written by the oracle alone): its state
+    at the iteration t_stop where its X^t first met infeasibility <= 1e-6, and the
+    <C, X> there.  Each GPU path runs as a user would run it (K from its own cost) from
+    the Alg. 2 start: to t_stop (errors of nu, theta, log Z, <C, X> at the same t), and
+    to its own tolerance (cost at tolerance and iterations)."""
+    import oracle as O
+    import workloads as W
+
+    z = np.load(GOLDEN_STATES)
+    n = int(z["n"])
+    w = W.highdim(seed=int(z["seed"]))
+    x, y = np.ascontiguousarray(w.x[:n]), np.ascontiguousarray(w.y[:n])
+    r = W.uniform_marginal(n)
+    c = W.uniform_marginal(n)
+    C = O.sqeuclid_cost_expanded(x, y)
+    K = float(z["fp32_K"])
+    T = int(z["fp32_t_stop"])
+    nu_T, th_T, kap_T = z["fp32_nu_stop"], z["fp32_theta_stop"], float(z["fp32_kappa_stop"])
+    col_T, logZ_T = O.marginals_from_state(C, r, K, kap_T, nu_T)
+    X = r[:, None] * O.dual_to_primal(C, K, kap_T, nu_T)[0]
+    cost_T = float((C * X).sum())
+    del X
+    Cb = O.sqeuclid_cost_expanded(W.bf16_round(x), W.bf16_round(y))
+    pert = float(np.abs(Cb - C).max())
+    del Cb
+    out = {"sample": f"first {n} x {n} supports of the highdim workload, uniform marginals, eta = 0",
+           "oracle": {"t_stop": T, "cost_at_t_stop": cost_T, "cost_at_tol": float(z["fp32_cost_stop"]),
+                      "K": K},
+           "bf16_cost_perturbation_max": pert,
+           "bf16_cost_perturbation_note": "max_ij |C(bf16-rounded points) - C|: bounds |OT(C~) - OT(C)|"}
+    t_ = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(devc)
+    xs, ys, rs, cs = t_(x), t_(y), t_(r), t_(c)
+    for prec in ("bf16_tc", "fp32"):
+        s = L.Lamp(rs, cs, x=xs, y=ys, cost_scale=1.0, prec=prec, check_every=50)
+        s.iterate(T)
+        obj = s.objective()
+        st = s.get_state()
+        lz_err = float((np.abs(st["logZ"] - logZ_T) / (1.0 + np.abs(logZ_T))).max())
+        rec = {"at_t_stop": {"nu_max_abs_err": float(np.abs(st["nu"] - nu_T).max()),
+                             "theta_max_abs_err": float(np.abs(st["theta"] - th_T).max()),
+                             "logZ_max_rel_err": lz_err,
+                             "cost_rel_err": abs(obj["cost"] - cost_T) / abs(cost_T),
+                             "infeas_gpu": obj["col_res"], "K_gpu": obj["K"]}}
+        s.close()
+        s = L.Lamp(rs, cs, x=xs, y=ys, cost_scale=1.0, prec=prec, tol=1e-6, check_every=50)
+        res = s.solve()
+        cat = s.objective()["cost"]
+        s.close()
+        rec["at_tol"] = {"iters": res["iters"], "oracle_iters": T, "converged": res["converged"],
+                         "cost_at_tol": cat,
+                         "cost_at_tol_rel_err": abs(cat - float(z["fp32_cost_stop"])) / abs(float(z["fp32_cost_stop"]))}
+        out[prec] = rec
+    return out
+
+
 def run_reference(args, rank, world):
     """--impl reference: the FP64 CPU oracle as it stands, on the host cores."""
     if rank != 0:
@@ -403,6 +465,8 @@ def run_gpu(args, rank, world):
                                      "grad_finite": bool(torch.isfinite(xg.grad).all() and torch.isfinite(yg.grad).all())}
 
     clocks = sampler.stop()
+    if rank == 0 and args.workload == "highdim" and not args.no_precision and w.n == 1 << 15:
+        info["precision_vs_fp64_oracle"] = precision_report(L, torch, devc)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -535,6 +599,8 @@ def main():
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-infeasibility measurement")
     ap.add_argument("--ttt-max-iter", type=int, default=200000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the error report of both GPU precisions against the FP64 oracle (highdim)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-points", type=int, default=2048)
     ap.add_argument("--lse-table", action="store_true",

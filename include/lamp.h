@@ -236,9 +236,15 @@ LAMP_API int lamp_round(lamp_ctx* ctx, double out[4], double* y, double* delta_r
  * to the points (envelope theorem): dL/dx_i = sum_j X_ij dC_ij/dx_i and
  * dL/dy_j = sum_i X_ij dC_ij/dy_j, with dC_ij/dx_i = 2 s (x_i - y_j).
  * dx: device n x d float32, dy: device m x d float32 (either may be NULL).
- * One evaluation pass, then ceil(d / 8) recompute sweeps per side (X never stored).
- * With LAMP_PREC_BF16_TC the points are the bf16-rounded ones the context solves
- * with.  SQEUCLID only (LAMP_E_UNSUPPORTED otherwise).  Asynchronous. */
+ * One evaluation pass, then per side one recompute pass (X never stored):
+ *   LAMP_PREC_FP32: ceil(d / 8) float32 sweeps per side (chunks of 8 coordinates);
+ *   LAMP_PREC_BF16_TC: one tensor-core pass per side on the bf16-rounded points the
+ *   context solves with: S = x.y^T by tcgen05, the coupling's entries formed in the
+ *   epilogue and split into two bf16 parts (16 significant bits), sum_j X_ij y_j by a
+ *   second tcgen05 MMA with float32 accumulation; the first call allocates transposed
+ *   bf16 copies of the points (O((n + m) 64)) and float32 partial sums (O((n + m) 64)
+ *   per inner split).
+ * SQEUCLID only (LAMP_E_UNSUPPORTED otherwise).  Asynchronous. */
 LAMP_API int lamp_grad(lamp_ctx* ctx, float* dx, float* dy);
 
 /* Copy the state to host memory (synchronises).  nu, theta: m doubles; logZ:

@@ -20,8 +20,8 @@ INCLUDE = ROOT / "include"
 BUILD = ROOT / "_build"
 LIB = PKG / "liblamp.so"
 
-SOURCES = ["lamp_kernels.cu", "lamp_api.cu", "lamp_noalloc.cu", "lamp_tc.cu", "lamp_probe.cu", "lamp_eval.cu", "lamp_direct.cu",
-           "lamp_dense.cu"]
+SOURCES = ["lamp_kernels.cu", "lamp_api.cu", "lamp_noalloc.cu", "lamp_tc.cu", "lamp_tc_grad.cu", "lamp_probe.cu",
+           "lamp_eval.cu", "lamp_direct.cu", "lamp_dense.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

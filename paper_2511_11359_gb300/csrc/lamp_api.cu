@@ -55,6 +55,15 @@ struct lamp_ctx {
   alignas(64) unsigned char map_x64[128];
   alignas(64) unsigned char map_y64[128];
   alignas(64) unsigned char map_c[128];  // stored cost (TMA-fed sweeps)
+  // tensor-core gradient pass (LAMP_PREC_BF16_TC, |x - y|^2): transposed bf16 copies of the
+  // points (64 x n_pad, 64 x m_pad), their tensor maps and the float32 partial sums
+  void* xT = nullptr;
+  void* yT = nullptr;
+  bool tcg_fresh = false;  // the transposed copies match the current bf16 points
+  float* tcg_part = nullptr;
+  size_t tcg_part_floats = 0;
+  alignas(64) unsigned char map_xT[128];
+  alignas(64) unsigned char map_yT[128];
   std::string err;
 };
 
@@ -840,9 +849,60 @@ static int objective_values(lamp_ctx* ctx, double* out) {
   return LAMP_OK;
 }
 
+static inline int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// the envelope gradient on tensor cores: one fused recompute pass per side (S = x.y^T by
+// MMA, P = 2^v w in the epilogue, P.Y by a second MMA), then a float64 finalize
+static int grad_tc(lamp_ctx* ctx, float* dx, float* dy) {
+  const Consts& k = ctx->k;
+  const int64_t n_pad = tc_pad(k.n), m_pad = tc_pad(k.m);
+  const int64_t wave = (int64_t)ctx->g.sms * 2;  // two CTAs per SM
+  const int sx = choose_split(cdiv64(k.n, tcg_tile_fixed()), cdiv64(k.m, tcg_tile_stream()), wave, 4);
+  const int sy = choose_split(cdiv64(k.m, tcg_tile_fixed()), cdiv64(k.n, tcg_tile_stream()), wave, 4);
+  int rc;
+  if (!ctx->xT) {
+    CK(tcg_prepare());
+    if ((rc = dalloc(ctx, reinterpret_cast<uint16_t**>(&ctx->xT), (size_t)n_pad * 64))) return rc;
+    if ((rc = dalloc(ctx, reinterpret_cast<uint16_t**>(&ctx->yT), (size_t)m_pad * 64))) return rc;
+    CK(tc_make_map2(ctx->map_xT, ctx->xT, n_pad, 64, 64, 64));
+    CK(tc_make_map2(ctx->map_yT, ctx->yT, m_pad, 64, 64, 64));
+    ctx->tcg_fresh = false;
+  }
+  const size_t need = (size_t)std::max<int64_t>((int64_t)sx * k.n, (int64_t)sy * k.m) * 64;
+  if (need > ctx->tcg_part_floats) {
+    if (ctx->tcg_part) {
+      CK(cudaStreamSynchronize(ctx->stream));
+      auto it = std::find(ctx->allocs.begin(), ctx->allocs.end(), (void*)ctx->tcg_part);
+      if (it != ctx->allocs.end()) ctx->allocs.erase(it);
+      cudaFree(ctx->tcg_part);
+      ctx->tcg_part = nullptr;
+      ctx->tcg_part_floats = 0;
+    }
+    if ((rc = dalloc(ctx, &ctx->tcg_part, need))) return rc;
+    ctx->tcg_part_floats = need;
+  }
+  if (!ctx->tcg_fresh) {
+    CK(tcg_transpose(ctx->xb, n_pad, ctx->xT, ctx->stream));
+    CK(tcg_transpose(ctx->yb, m_pad, ctx->yT, ctx->stream));
+    ctx->tcg_fresh = true;
+  }
+  if ((rc = evaluate(ctx))) return rc;
+  const int cur = ctx->host_dev->cur;
+  if (dx) {
+    CK(tcg_launch(true, ctx->map_x, ctx->map_y64, ctx->map_yT, ctx->w, k, sx, ctx->tcg_part, ctx->stream));
+    CK(tcg_finalize(true, ctx->tcg_part, sx, ctx->w, k, ctx->in.x, ctx->in.r, ctx->w.g2row, dx, ctx->stream));
+  }
+  if (dy) {
+    CK(tcg_launch(false, ctx->map_y, ctx->map_x64, ctx->map_xT, ctx->w, k, sy, ctx->tcg_part, ctx->stream));
+    CK(tcg_finalize(false, ctx->tcg_part, sy, ctx->w, k, ctx->in.y, ctx->in.r, ctx->w.colq[cur], dy, ctx->stream));
+  }
+  return LAMP_OK;
+}
+
 extern "C" int lamp_grad(lamp_ctx* ctx, float* dx, float* dy) {
   if (!ctx) return fail(nullptr, LAMP_E_INVALID, "lamp_grad: null context");
   if (ctx->pub_kind != LAMP_COST_SQEUCLID) return fail(ctx, LAMP_E_UNSUPPORTED, "lamp_grad needs LAMP_COST_SQEUCLID");
+  if (ctx->prec == LAMP_PREC_BF16_TC) return grad_tc(ctx, dx, dy);
   // d > 8: the gradient is computed in chunks of 8 coordinates (partials of 8 values per point)
   int rc = ensure_part_width(ctx, std::min<int>((int)ctx->k.d, 8));
   if (rc) return rc;
@@ -936,6 +996,7 @@ extern "C" int lamp_step_host(lamp_ctx* ctx, const float* C_or_x, const float* y
   if (ctx->prec == LAMP_PREC_BF16_TC) {
     CK(tc_convert(px, k.n, k.d, ctx->xr, ctx->xb, ctx->stream));
     CK(tc_convert(py, k.m, k.d, ctx->yr, ctx->yb, ctx->stream));
+    ctx->tcg_fresh = false;  // the gradient pass transposes the new points on its next call
   }
   int rc = lamp_iterate(ctx, iters);
   if (rc) return rc;

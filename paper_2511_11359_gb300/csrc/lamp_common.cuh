@@ -407,6 +407,20 @@ int dense_tile_cols();
 int dense_blocks_per_sm();
 cudaError_t dense_launch_sweep(bool rows, int eval, const Geometry& g, const Work& w, const Consts& k, int splits,
                                cudaStream_t st);
+// tensor-core gradient pass (lamp_tc_grad.cu): transposed bf16 copies (64 x np_pad), one side
+// of the pass (float32 partials [splits][np][64]) and its finalize
+size_t tcg_smem_bytes();
+cudaError_t tcg_prepare();
+cudaError_t tcg_transpose(const void* Pb, int64_t np_pad, void* PT, cudaStream_t st);
+int tcg_tile_fixed();
+int tcg_tile_stream();
+cudaError_t tcg_launch(bool rows, const void* map_fixed, const void* map_stream, const void* map_streamT,
+                       const Work& w, const Consts& k, int splits, float* part, cudaStream_t st);
+cudaError_t tcg_finalize(bool rows, const float* part, int splits, const Work& w, const Consts& k, const float* P,
+                         const double* r, const float4* wsrc, float* out, cudaStream_t st);
+// 2-D bf16 tensor map over a row-major (rows x inner) array with box_inner x box_rows boxes
+// and 128-byte swizzle (inner * 2 bytes a multiple of 16)
+cudaError_t tc_make_map2(void* map_out, const void* base, int64_t inner, int64_t rows, int box_inner, int box_rows);
 int tc_tile_fixed();   // points of the fixed tile of a tensor-core sweep
 int tc_tile_stream();  // points of a streamed tile
 cudaError_t tc_prepare();

@@ -32,6 +32,7 @@
 
 #include "lamp_async.cuh"
 #include "lamp_common.cuh"
+#include "lamp_tc.cuh"
 
 namespace lamp {
 
@@ -89,45 +90,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, Bars* 
   return async::mbar_wait(bar, parity, &B->err, dev, limit);
 }
 
-__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_relinquish() {
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-
-// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (bf16 in, fp32 accumulate)
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                          uint32_t accumulate) {
-  asm volatile(
-      "{\n"
-      ".reg .pred p;\n"
-      "setp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
-      "}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-
 // 8 consecutive FP32 columns of this warp's 32 TMEM lanes at two addresses (the two
 // accumulator halves), without waiting: tcgen05.ld writes its destination registers
 // asynchronously, until tcgen05.wait::ld.
@@ -172,30 +134,6 @@ __device__ __forceinline__ bool epi_bar_or(bool v) {
 }
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
-
-// Shared-memory matrix descriptor of a K-major bf16 tile written by TMA with
-// 128-byte swizzle: rows of 128 bytes, 8-row (1024-byte) swizzle atoms, so the
-// stride between 8-row groups is 1024 bytes; the leading offset is unused for
-// this layout; bits 46-47 hold the descriptor version 1; layout type 2 = 128B
-// swizzle.  Stepping K by 16 elements advances the start address by 32 bytes.
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-// Instruction descriptor, kind::f16: D fp32, A and B bf16, both K-major, M = 128, N = 64.
-__host__ __device__ constexpr uint32_t idesc_bf16_128x64() {
-  return (1u << 4)                        // D format: f32
-         | (1u << 7)                      // A format: bf16
-         | (1u << 10)                     // B format: bf16
-         | ((uint32_t)(kStream >> 3) << 17)  // N >> 3
-         | ((uint32_t)(kTile >> 4) << 24);   // M >> 4
-}
 
 // ROWS = true: G1 (fixed x tile, streamed y tiles, per-row sums of both streams)
 // ROWS = false: G2 (fixed y tile, streamed x tiles, per-column sums of both streams)
@@ -286,7 +224,7 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
   } else if (warp == kMmaWarp) {
     // ------ MMA issuer: D[buffer][half a] = A(fixed half a) * B(streamed)^T, a = 0, 1 ------
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16_128x64();
+      const uint32_t idesc = idesc_bf16(kTile, kStream);
       int issued = 0;
       if (mbar_wait(&B->fixed_full, 0, B, dev)) {
         const uint32_t sF = smem_u32(sFixed);
@@ -559,6 +497,10 @@ cudaError_t tc_fill_pairs(float4* a, int64_t count, cudaStream_t st) {
 // encode a 2-D bf16 tensor map over a (rows_pad x 64) row-major array, box_rows x 64 boxes,
 // 128B swizzle (box_rows: 128 for the fixed halves, 64 for the streamed tiles)
 cudaError_t tc_make_map(void* map_out, const void* base, int64_t rows_pad, int box_rows) {
+  return tc_make_map2(map_out, base, tc::kK, rows_pad, tc::kK, box_rows);
+}
+
+cudaError_t tc_make_map2(void* map_out, const void* base, int64_t inner, int64_t rows, int box_inner, int box_rows) {
   typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -570,9 +512,9 @@ cudaError_t tc_make_map(void* map_out, const void* base, int64_t rows_pad, int b
     if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) return cudaErrorNotSupported;
     fn = reinterpret_cast<EncodeFn>(p);
   }
-  cuuint64_t dims[2] = {(cuuint64_t)tc::kK, (cuuint64_t)rows_pad};
-  cuuint64_t strides[1] = {(cuuint64_t)tc::kK * 2};
-  cuuint32_t box[2] = {(cuuint32_t)tc::kK, (cuuint32_t)box_rows};
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)inner * 2};
+  cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base),
                   dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
