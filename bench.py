@@ -441,6 +441,7 @@ def run_gpu(args, rank, world):
         info["time_to_tol"] = {"seconds": el, "iters": res["iters"], "infeas": res["infeas"],
                                "converged": res["converged"], "tol": w.tol}
         info["cost_at_tol"] = s2.objective()["cost"]
+        s2_state = s2.get_state()
         s2.close()
         if w.kind != "dense":
             # the autograd form: lamp_ot_loss forward (context creation, solve to tol, objective)
@@ -463,6 +464,23 @@ def run_gpu(args, rank, world):
             info["autograd_form"] = {"forward_s": t1 - t0, "backward_s": t2 - t1, "total_s": t2 - t0,
                                      "loss": float(loss.item()),
                                      "grad_finite": bool(torch.isfinite(xg.grad).all() and torch.isfinite(yg.grad).all())}
+            # lamp_grad alone on the converged context of the timed solve (s2 was closed: a fresh
+            # context on its final state), first call (allocates its buffers) and a repeat
+            sg = L.Lamp(r, c, x=x, y=y, cost_scale=w.cost_scale, **params)
+            st2 = s2_state
+            sg.set_state(st2["nu"], st2["theta"], st2["kappa"], st2["t"], st2["row_shifts"])
+            gms = []
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                sg.grad()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                gms.append(e0.elapsed_time(e1))
+            sg.close()
+            info["autograd_form"]["lamp_grad_ms"] = {"first_call": gms[0], "repeat": min(gms[1:]),
+                                                     "includes": "one evaluation pass + one pass per side"}
 
     clocks = sampler.stop()
     if rank == 0 and args.workload == "highdim" and not args.no_precision and w.n == 1 << 15:

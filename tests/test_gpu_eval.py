@@ -251,7 +251,8 @@ def test_solve_stops_on_the_primal_dual_gap(eta):
     assert res["stop"] == "gap" and res["gap"] <= gap_tol, res
     obj = sol.objective()  # the same state: the same gap
     assert obj["gap"] == pytest.approx(res["gap"], rel=0, abs=1e-12 * K)
-    assert obj["dual"] <= ref + 1e-9 * K, (obj["dual"], ref)
+    # the dual's own error: ~1e-12 K at eta = 0, the ex2 error ~2^-22 eta of the softmin at eta > 0
+    assert obj["dual"] <= ref + 1e-9 * K + 4e-7 * eta, (obj["dual"], ref)
     assert ref <= obj["P_eta"] + 2e-7 * K, (obj["P_eta"], ref)
     assert obj["P_eta"] - ref <= gap_tol + 1e-9 * K
     sol.close()

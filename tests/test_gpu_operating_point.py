@@ -87,9 +87,11 @@ def test_step_and_evaluation_at_headline_kappa(prec, T0):
     got = sol.get_state()
     dnu = np.abs(got["nu"] - ref1.nu).max()
     dth = np.abs(got["theta"] - ref1.theta).max()
-    xs = W.bf16_round(w.x) if variant == "bf16" else w.x
-    ys = W.bf16_round(w.y) if variant == "bf16" else w.y
-    tol = POT_TOL + _dot_slack(xs, ys, st0.kappa)
+    # tensor cores: the products of bf16 points are exact and the MMA's float32 accumulation
+    # keeps the potentials within the plain 1e-5 (measured 2.3e-6 at t = 500, 6.7e-6 at
+    # t = 1170); the float32 dot form rounds every product and partial sum, so its potentials
+    # move by up to ~kappa |delta| (measured 7.6e-6 at t = 500, 1.9e-5 at t = 1170)
+    tol = POT_TOL if prec == "bf16_tc" else POT_TOL + _dot_slack(w.x, w.y, st0.kappa)
     print(f"\n{prec} T0={T0}: |dnu|={dnu:.3e} |dtheta|={dth:.3e} tol={tol:.3e} (plain {POT_TOL:.0e})")
     assert dnu <= tol and dth <= tol
     # evaluation of X^{T0+1} from the oracle's state (log Z and <C, X>)
@@ -101,7 +103,7 @@ def test_step_and_evaluation_at_headline_kappa(prec, T0):
     cost_err = abs(obj["cost"] - rep["cost"]) / abs(rep["cost"])
     print(f"{prec} T0={T0}: logZ rel err {lz_err:.3e}, <C,X> rel err {cost_err:.3e}, "
           f"res gpu {obj['col_res']:.4e} oracle {rep['col_res']:.4e}")
-    assert lz_err <= LOGZ_TOL + tol
+    assert lz_err <= (LOGZ_TOL if prec == "bf16_tc" else LOGZ_TOL + tol)
     assert cost_err <= OBJ_TOL
     sol.close()
 
