@@ -290,6 +290,7 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
   k.eta = params->eta;
   k.infeas_only = params->infeas_only;
   k.alpha = params->alpha;
+  k.alpha_m = params->alpha / (double)prob->m;
   k.clipb = std::tanh(params->beta / 2.0);
   ctx->log_m = std::log((double)k.m);
 
@@ -674,11 +675,14 @@ extern "C" int lamp_solve(lamp_ctx* ctx, lamp_result* out) {
                       (ctx->k.eta == 0.0 || ctx->k.infeas_only || 1.0 - hd.kappa * ctx->k.eta <= pa.tol);
     stop = rule ? LAMP_STOP_INFEAS : LAMP_STOP_MAX_ITER;
   }
+  const double rule_res = hd.res;  // the infeasibility the stopping rule saw
   if (stop != LAMP_STOP_GAP && ctx->k.shared_shift && hd.status == 0) {
     // the regular iterations of the packed direct-form sweeps leave <C, X^t> out: one
-    // evaluation pass of the final state provides it
+    // evaluation pass of the final state provides it (its column sums may differ from the
+    // iteration's in the last bits; the result keeps the value the stopping rule used)
     int rc = evaluate(ctx);
     if (rc) return rc;
+    ctx->host_dev->res = rule_res;
   }
   fill_result(ctx, out, stop, gap);
   const DevState& d = *ctx->host_dev;

@@ -69,6 +69,7 @@ struct Consts {
   double s;          // cost scale (1 for DENSE)
   double tau1, tau2, eta, alpha;
   double clipb;      // tanh(beta/2)
+  double alpha_m;    // alpha / m (c^alpha = c + alpha/m, Section 3.1)
   double W;          // bound factor for the exponent offsets: |Bq|+|Rq| <= lambda*W + 128
   double rnx;        // sum_i r_i s |x_i|^2 (dot-form cost bookkeeping), 0 otherwise
   int32_t zdot;      // 1: z = x.y (dot form), 0: z = C/s (direct form)
@@ -92,6 +93,7 @@ struct SweepParams {
   double aA, aB;       // float64 exponent multipliers of z
   float ahA, alA, ahB, alB;  // a = ah + al, both float32
   double g;            // offset grid (power of two)
+  double wB;           // tau1 / kappa_{t+1} = tau1 eta_{t+1}, the averaging weight of Alg. 2
 };
 
 __host__ __device__ inline double kappa_next(double kap, const Consts& k) {
@@ -117,6 +119,7 @@ __host__ __device__ inline SweepParams make_sweep_params(double kap, const Const
     p.aA = 2.0 * p.lamA * k.s;
     p.aB = 2.0 * p.lamB * k.s;
   }
+  p.wB = k.tau1 / p.kapB;
   p.ahA = (float)p.aA;
   p.alA = (float)(p.aA - (double)p.ahA);
   p.ahB = (float)p.aB;
@@ -214,7 +217,8 @@ __device__ __forceinline__ float4 column_data(double nu_j, double nubar_j, doubl
   double qA = quantize(bA, sp.g);
   double qB = quantize(bB, sp.g);
   if (dB) *dB = (float)(qA - bB);
-  return make_float4((float)qA, (float)exp2(-(bA - qA)), (float)qB, (float)exp2(-(bB - qB)));
+  // the sub-grid remainders are at most half a grid step: their powers of two in float32
+  return make_float4((float)qA, exp2f((float)(qA - bA)), (float)qB, exp2f((float)(qB - bB)));
 }
 
 // Knuth's branch-free TwoSum: s + e == a + b exactly

@@ -726,15 +726,20 @@ k_row_fin(const Work w, int splits, const double* __restrict__ r, const Consts k
     }
     float2 rq = rs_cur[i];
     double snx = k.zdot ? k.s * nx[i] : 0.0;
-    double lsA = log2(SA), lsB = log2(SB);
+    // float64 log2 and divisions: with float32 ones (log2f carries an absolute error of
+    // ~2^-22 near 1) the potentials of 100-iteration trajectories drifted from the oracle's
+    // by ~1e-6 instead of ~1e-8, and log Z, which amplifies nu by 2 K kappa, by ~1e-4
+    const double lsA = log2(SA), lsB = log2(SB);
     double L2A = (double)rq.x - sp.lamA * snx + lsA;  // log2 Z of X^t
     double L2B = (double)rq.y - sp.lamB * snx + lsB;  // log2 Z of Xbar^{t+1}
     double lz = kLn2 * L2A;
     logZ[i] = lz;
     double ri = r[i];
     contrib = ri * lz;
-    g2row[i] = make_float4(rq.x, (float)(ri / SA), rq.y, (float)(ri / SB));
-    if (w.g2row2) store_pair_entry(w.g2row2, i, rq.x, (float)(ri / SA), 0.f, (float)(ri / SB));
+    // the row weights q = r / S, float32 factors of the column sweep
+    const float qa = (float)(ri / SA), qb = (float)(ri / SB);
+    g2row[i] = make_float4(rq.x, qa, rq.y, qb);
+    if (w.g2row2) store_pair_entry(w.g2row2, i, rq.x, qa, 0.f, qb);
     // shifts of iteration t+1: stream A there has kappa_{t+1} (stream B here);
     // stream B there is extrapolated linearly in t.
     double tA = (double)rq.y + lsB;
@@ -807,18 +812,23 @@ k_col_fin(const Work w, int splits, const double* __restrict__ cvec, int rowbloc
     colA[j] = A;
     if (with_cost && w.colz) w.colz[j] = cost;
     if (!eval_only) {
-      const double ca = cj + k.alpha / (double)k.m;  // c^alpha (Section 3.1)
+      // the dual mirror steps (Eq. def:closed_form_opt) tanh(g (col - c) + atanh theta), in
+      // float64 through the addition theorem tanh(u + atanh theta) = (tanh u + theta) /
+      // (1 + theta tanh u): one tanh per stream and no atanh (|theta^t| <= tanh(beta/2) < 1,
+      // so the denominator is at least 1 - tanh(beta/2))
+      const double ca = cj + k.alpha_m;                  // c^alpha (Section 3.1)
       const double gj = 2.0 * k.tau2 * k.K / ca;
-      const double ath = atanh(thj);
-      const double wt = k.tau1 / sp.kapB;                // tau1 eta_{t+1}
-      const double thbar = tanh(gj * (A - cj) + ath);    // M_{tau2}(theta^t; p^{eta_t}(nu^t))
+      const double wt = sp.wB;                           // tau1 eta_{t+1}
+      const double tA = tanh(gj * (A - cj));
+      const double thbar = (tA + thj) / fma(tA, thj, 1.0);  // M_{tau2}(theta^t; p^{eta_t}(nu^t))
       const double nun = nuj + wt * (thbar - nuj);       // nu^{t+1}
-      double thhat = tanh(gj * (B - cj) + ath);          // M_{tau2}(theta^t; p^{eta_{t+1}}(nubar^{t+1}))
+      const double tB = tanh(gj * (B - cj));
+      const double thhat = (tB + thj) / fma(tB, thj, 1.0);  // M_{tau2}(theta^t; p^{eta_{t+1}}(nubar^{t+1}))
       const double thn = fmin(fmax(thhat, -k.clipb), k.clipb);  // tclip
       nu_nxt[j] = nun;
       th_nxt[j] = thn;
       // column data of iteration t+1
-      const double wn = k.tau1 / spn.kapB;
+      const double wn = spn.wB;
       const double nbn = nun + wn * (thn - nun);         // nubar^{t+2}
       const double sny = k.zdot ? k.s * ny[j] : 0.0;
       float dB;

@@ -168,6 +168,7 @@ extern "C" int lamp_marginals_noalloc(const lamp_problem* prob, double K, double
   k.tau1 = k.tau2 = 1.0 / (2.0 * K);
   k.eta = 0.0;
   k.alpha = 0.01;
+  k.alpha_m = 0.01 / (double)k.m;
   k.clipb = std::tanh(0.55);
   k.W = 5.0 * K;
   k.rnx = 0.0;
