@@ -198,3 +198,40 @@ def test_largescale_recipe_trajectory_at_2_14():
     res = float(np.abs(colT - w.c).sum())
     assert abs(obj["col_res"] - res) <= 1e-6 * res + RES_FLOOR
     s.close()
+
+
+def test_precision_against_the_unrounded_problem():
+    """The error each GPU precision makes against the FP64 oracle on the unrounded problem
+    (the 4096 x 4096 sample; the oracle's state at its stop t = 1269 from the golden file),
+    both paths run as a user runs them (K from their own cost) for the same t.
+    Bounds stated here (measured values in parentheses):
+      float32 dot form   potentials <= 2e-5 (3.1e-6), <C, X> <= 1e-7 relative (1.8e-9);
+      bf16 tensor cores  potentials <= 2e-3 (3.7e-4), <C, X> <= 5e-5 relative (8.4e-6):
+        the bf16 rounding of the points moves C by up to 0.55 (0.18 % of K) and the
+        trajectory with it; the objective moves far less because the rounding errors
+        average over the plan.
+    Both paths reach infeasibility <= 1e-6 within 1 % of the oracle's iteration count."""
+    import paper_2511_11359_gb300 as L
+
+    g, w, C = _sample("fp32")
+    T = int(g["fp32_t_stop"])
+    nu_T, th_T, kap_T = g["fp32_nu_stop"], g["fp32_theta_stop"], float(g["fp32_kappa_stop"])
+    K = float(g["fp32_K"])
+    X = w.r[:, None] * O.dual_to_primal(C, K, kap_T, nu_T)[0]
+    cost_T = float((C * X).sum())
+    del X
+    bounds = {"fp32": (2e-5, 1e-7), "bf16_tc": (2e-3, 5e-5)}
+    for prec, (pot_b, cost_b) in bounds.items():
+        s = L.Lamp(dev(w.r), dev(w.c), x=dev(w.x), y=dev(w.y), cost_scale=1.0, prec=prec, check_every=50)
+        s.iterate(T)
+        obj = s.objective()
+        st = s.get_state()
+        s.close()
+        dpot = max(np.abs(st["nu"] - nu_T).max(), np.abs(st["theta"] - th_T).max())
+        dcost = abs(obj["cost"] - cost_T) / cost_T
+        print(f"\n{prec}: potentials {dpot:.3e}, <C,X> rel {dcost:.3e}")
+        assert dpot <= pot_b and dcost <= cost_b
+        s = L.Lamp(dev(w.r), dev(w.c), x=dev(w.x), y=dev(w.y), cost_scale=1.0, prec=prec, tol=1e-6, check_every=50)
+        res = s.solve(allow_not_converged=False)
+        s.close()
+        assert abs(res["iters"] - T) <= 0.01 * T, res["iters"]
