@@ -236,7 +236,8 @@ LAMP_API int lamp_round(lamp_ctx* ctx, double out[4], double* y, double* delta_r
  * to the points (envelope theorem): dL/dx_i = sum_j X_ij dC_ij/dx_i and
  * dL/dy_j = sum_i X_ij dC_ij/dy_j, with dC_ij/dx_i = 2 s (x_i - y_j).
  * dx: device n x d float32, dy: device m x d float32 (either may be NULL).
- * One evaluation pass, then per side one recompute pass (X never stored):
+ * One evaluation pass (skipped when the state's X^t was the last one evaluated, e.g. after
+ * lamp_solve or lamp_objective), then per side one recompute pass (X never stored):
  *   LAMP_PREC_FP32: ceil(d / 8) float32 sweeps per side (chunks of 8 coordinates);
  *   LAMP_PREC_BF16_TC: one tensor-core pass per side on the bf16-rounded points the
  *   context solves with: S = x.y^T by tcgen05, the coupling's entries formed in the

@@ -166,7 +166,7 @@ static int validate(const lamp_problem* pr, const lamp_params* pa, bool device_p
   return LAMP_OK;
 }
 
-static int choose_split(int64_t tout, int64_t tin, int64_t wave, int64_t min_inner) {
+static int choose_split(int64_t tout, int64_t tin, int64_t wave, int64_t min_inner, double per_split = 0.002) {
   int best = 1;
   double best_score = -1.0;
   int64_t smax = std::min<int64_t>(std::max<int64_t>(tin / std::max<int64_t>(min_inner, 1), 1), 128);
@@ -174,7 +174,7 @@ static int choose_split(int64_t tout, int64_t tin, int64_t wave, int64_t min_inn
     int64_t ctas = tout * s;
     int64_t waves = (ctas + wave - 1) / wave;
     double util = (double)ctas / (double)(waves * wave);
-    double score = util - 0.002 * s;
+    double score = util - per_split * s;
     if (score > best_score + 1e-12) {
       best_score = score;
       best = s;
@@ -731,6 +731,18 @@ static int evaluate(lamp_ctx* ctx) {
   return poll(ctx);
 }
 
+// the gradient passes need the row weights, column data and col(X^t) of the current state:
+// when the last pass of the device loop (a stopped solve, lamp_objective) already evaluated
+// this X^t and nothing changed the state since (lamp_set_state resets t_eval), they are in
+// place and the evaluation pass is skipped
+static int evaluate_if_stale(lamp_ctx* ctx) {
+  int rc = poll(ctx);
+  if (rc) return rc;
+  const DevState& d = *ctx->host_dev;
+  if (d.t_eval == d.t && d.status == 0 && d.kappa_eval == d.kappa) return LAMP_OK;
+  return evaluate(ctx);
+}
+
 // run evaluation passes outside the iteration after an evaluate(): the sweeps return at
 // once while dev->done is set, so clear it for the passes and set it again after
 static int begin_passes(lamp_ctx* ctx) {
@@ -861,8 +873,10 @@ static int grad_tc(lamp_ctx* ctx, float* dx, float* dy) {
   const Consts& k = ctx->k;
   const int64_t n_pad = tc_pad(k.n), m_pad = tc_pad(k.m);
   const int64_t wave = (int64_t)ctx->g.sms * 2;  // two CTAs per SM
-  const int sx = choose_split(cdiv64(k.n, tcg_tile_fixed()), cdiv64(k.m, tcg_tile_stream()), wave, 4);
-  const int sy = choose_split(cdiv64(k.m, tcg_tile_fixed()), cdiv64(k.n, tcg_tile_stream()), wave, 4);
+  // every split writes 64 float32 partials per point: splits cost 1 % of a wave each here
+  // (0.2 % for the sweeps), which keeps their number near the smallest that fills the waves
+  const int sx = choose_split(cdiv64(k.n, tcg_tile_fixed()), cdiv64(k.m, tcg_tile_stream()), wave, 4, 0.01);
+  const int sy = choose_split(cdiv64(k.m, tcg_tile_fixed()), cdiv64(k.n, tcg_tile_stream()), wave, 4, 0.01);
   int rc;
   if (!ctx->xT) {
     CK(tcg_prepare());
@@ -890,7 +904,7 @@ static int grad_tc(lamp_ctx* ctx, float* dx, float* dy) {
     CK(tcg_transpose(ctx->yb, m_pad, ctx->yT, ctx->stream));
     ctx->tcg_fresh = true;
   }
-  if ((rc = evaluate(ctx))) return rc;
+  if ((rc = evaluate_if_stale(ctx))) return rc;
   const int cur = ctx->host_dev->cur;
   if (dx) {
     CK(tcg_launch(true, ctx->map_x, ctx->map_y64, ctx->map_yT, ctx->w, k, sx, ctx->tcg_part, ctx->stream));
@@ -910,7 +924,7 @@ extern "C" int lamp_grad(lamp_ctx* ctx, float* dx, float* dy) {
   // d > 8: the gradient is computed in chunks of 8 coordinates (partials of 8 values per point)
   int rc = ensure_part_width(ctx, std::min<int>((int)ctx->k.d, 8));
   if (rc) return rc;
-  rc = evaluate(ctx);
+  rc = evaluate_if_stale(ctx);
   if (rc) return rc;
   CK(launch_grad(ctx->in, ctx->k, ctx->w, ctx->g, ctx->prec, dx, dy, ctx->stream));
   return LAMP_OK;

@@ -125,6 +125,13 @@ __device__ __forceinline__ void tmem_st16(uint32_t ta, const uint32_t (&v)[16]) 
       : "memory");
 }
 
+// 8 consecutive 32-bit columns of this warp's 32 lanes from registers
+__device__ __forceinline__ void tmem_st8(uint32_t ta, const uint32_t (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(ta), "r"(v[0]),
+               "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
+}
+
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // 32 FP32 columns of this warp's 32 lanes, waited for
@@ -314,42 +321,52 @@ k_tc_grad(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant__
       tc_fence_after();
       const float4* pr = sPair + (size_t)b * kStream;
       const uint32_t tbase = tmem + lane_base + b * kStream + h * kSliceCols;
-      uint32_t phi[16], plo[16];
+      // two halves of 16 columns: P of the first half is stored once the previous tile's MMA 2
+      // has read P (by then long done), so no wait stalls the start of a tile, and only 8
+      // words of each part are held in registers
       uint32_t vv[2][8];
       tmem_ld8(tbase, vv[0]);
       tmem_wait_ld8(vv[0]);
 #pragma unroll
-      for (int c = 0; c < kSliceCols / 8; ++c) {
-        if (c + 1 < kSliceCols / 8) tmem_ld8(tbase + (c + 1) * 8, vv[(c + 1) & 1]);
-        const uint32_t(&v)[8] = vv[c & 1];
+      for (int half = 0; half < 2; ++half) {
+        uint32_t phi[8], plo[8];
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          const float4 q = pr[h * kSliceCols + c * 8 + 2 * p];  // {-off pair, weight pair}
-          const uint64_t z2 = pk(__uint_as_float(v[2 * p]), __uint_as_float(v[2 * p + 1]));
-          const float2 vA = upk(f2fma(ahA2, z2, f2add(own2, pk(q.x, q.y))));
-          const uint64_t P2 = f2mul(pk(ex2(vA.x), ex2(vA.y)), pk(q.z, q.w));
-          const float2 P = upk(P2);
-          const uint32_t hw = bf16x2(P.x, P.y);
-          const uint64_t hf = pk(__uint_as_float(hw << 16), __uint_as_float(hw & 0xffff0000u));
-          const float2 lo = upk(f2sub(P2, hf));  // exact: P - RN_bf16(P) has at most 16 significant bits
-          phi[c * 4 + p] = hw;
-          plo[c * 4 + p] = bf16x2(lo.x, lo.y);
+        for (int cc = 0; cc < 2; ++cc) {
+          const int c = 2 * half + cc;
+          if (c + 1 < kSliceCols / 8) tmem_ld8(tbase + (c + 1) * 8, vv[(c + 1) & 1]);
+          const uint32_t(&v)[8] = vv[c & 1];
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            const float4 q = pr[h * kSliceCols + c * 8 + 2 * p];  // {-off pair, weight pair}
+            const uint64_t z2 = pk(__uint_as_float(v[2 * p]), __uint_as_float(v[2 * p + 1]));
+            const float2 vA = upk(f2fma(ahA2, z2, f2add(own2, pk(q.x, q.y))));
+            const uint64_t P2 = f2mul(pk(ex2(vA.x), ex2(vA.y)), pk(q.z, q.w));
+            const float2 P = upk(P2);
+            const uint32_t hw = bf16x2(P.x, P.y);
+            const uint64_t hf = pk(__uint_as_float(hw << 16), __uint_as_float(hw & 0xffff0000u));
+            const float2 lo = upk(f2sub(P2, hf));  // exact: P - RN_bf16(P) has at most 16 significant bits
+            phi[cc * 4 + p] = hw;
+            plo[cc * 4 + p] = bf16x2(lo.x, lo.y);
+          }
+          if (c + 1 < kSliceCols / 8) tmem_wait_ld8(vv[(c + 1) & 1]);
         }
-        if (c + 1 < kSliceCols / 8) tmem_wait_ld8(vv[(c + 1) & 1]);
+        if (half == 0) {
+          // P of the previous tile has been consumed by its MMA 2 before it is overwritten
+          ok = i == 0 || mbar_wait(&B->p_empty, (i - 1) & 1, B, dev);
+          if (!__all_sync(0xffffffffu, ok)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+        }
+        tmem_st8(tmem + lane_base + kColPhi + h * (kSliceCols / 2) + half * 8, phi);
+        tmem_st8(tmem + lane_base + kColPlo + h * (kSliceCols / 2) + half * 8, plo);
       }
+      if (!ok) break;
       tc_fence_before();
       mbar_arrive(&B->s_empty[b]);
       fence_proxy_async_smem();  // the pair buffer was read through the generic proxy
       mbar_arrive(&B->pair_empty[b]);
-      // P of the previous tile has been consumed by its MMA 2 before it is overwritten
-      ok = i == 0 || mbar_wait(&B->p_empty, (i - 1) & 1, B, dev);
-      if (!__all_sync(0xffffffffu, ok)) {
-        ok = false;
-        break;
-      }
-      tc_fence_after();
-      tmem_st16(tmem + lane_base + kColPhi + h * (kSliceCols / 2), phi);
-      tmem_st16(tmem + lane_base + kColPlo + h * (kSliceCols / 2), plo);
       tmem_wait_st();
       tc_fence_before();
       mbar_arrive(&B->p_full);
@@ -405,8 +422,12 @@ __global__ void k_tc_grad_fin(const float* __restrict__ part, int splits, int64_
   if (e >= np * d) return;
   const int64_t i = e / d;
   const int q = (int)(e - i * d);
-  double acc = 0.0;
-  for (int sp = 0; sp < splits; ++sp) acc += (double)part[((int64_t)sp * np + i) * kK + q];
+  // the splits' partials are independent loads: issued together (unrolled), added in split
+  // order as a float-float pair (TwoSum), converted once
+  float hi = 0.f, lo = 0.f;
+#pragma unroll 8
+  for (int sp = 0; sp < splits; ++sp) ff_add(hi, lo, part[((int64_t)sp * np + i) * kK + q]);
+  const double acc = (double)hi + (double)lo;
   const double wgt = (double)wsrc[i].y;
   out[e] = (float)(2.0 * s * (mass[i] * (double)P[e] - wgt * acc));
 }
