@@ -57,8 +57,8 @@ def job_throughput(units_per_rank: float, local_seconds: float, dist=None, devic
 NCU_TRAFFIC = {
     ("highdim", "bf16_tc", 32768, 64): {
         "source": "paper_2511_11359_gb300/csrc/lamp_tc.cu",
-        "sha256": "7ab7588b802af7425939fad61349b35e6c75407a6212a2ef545656fe7ccc9ef2",
-        "row_sweep": 9223424, "col_sweep": 10010368},
+        "sha256": "ee6853d9906ab7d1f537ad7309f51ccfb5021d5897ef979de59d0544ed4f722c",
+        "row_sweep": 9223680, "col_sweep": 10012928},
     ("image_grid", "fp32", 4096, 0): {
         "source": "paper_2511_11359_gb300/csrc/lamp_dense.cu",
         "sha256": "0214d7ff91ff3f635ac75b39f297454933f9a9a9becf2116f747fecebaf78424",
@@ -600,6 +600,37 @@ def run_lse_table(args):
                       "warmup": args.warmup, "lse_table": rows}), flush=True)
 
 
+def run_grad_only(args):
+    """lamp_grad alone on the workload (tensor cores for d > 8): `warmup` iterations of Alg. 2,
+    then `steps` calls of lamp_grad on that state, each timed with CUDA events (the first call
+    also runs the evaluation pass and allocates the pass's buffers; later calls reuse both)."""
+    import torch
+    import paper_2511_11359_gb300 as L
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    w = make_workload(args.workload, 0, args.n)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    s = L.Lamp(t(w.r), t(w.c), x=t(w.x), y=t(w.y), cost_scale=w.cost_scale, eta=w.eta, prec=args.prec,
+               check_every=args.check_every)
+    s.iterate(args.warmup)
+    stream = torch.cuda.current_stream()
+    ms = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.grad()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    s.close()
+    print(json.dumps({"metric": "lamp_grad time (envelope gradient, both sides)", "unit": "ms",
+                      "higher_is_better": False, "workload": args.workload, "n": w.n, "m": w.m, "d": w.d,
+                      "prec": args.prec, "first_call_ms": ms[0],
+                      "repeat_ms": min(ms[1:]) if len(ms) > 1 else None, "calls": len(ms)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -621,6 +652,8 @@ def main():
                     help="skip the error report of both GPU precisions against the FP64 oracle (highdim)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-points", type=int, default=2048)
+    ap.add_argument("--grad-only", action="store_true",
+                    help="time lamp_grad alone (after --warmup iterations, --steps calls) instead of the bench")
     ap.add_argument("--lse-table", action="store_true",
                     help="row-sweep timings at the paper's Table 1 sizes (n = 1024 .. 65536) instead of the bench")
     args = ap.parse_args()
@@ -633,6 +666,8 @@ def main():
         raise SystemExit("--warmup must be >= 3")
     if args.lse_table:
         run_lse_table(args)
+    elif args.grad_only:
+        run_grad_only(args)
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
