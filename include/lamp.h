@@ -290,8 +290,9 @@ LAMP_API int lamp_time_kernels(lamp_ctx* ctx, int64_t iters, double* ms_out);
 LAMP_API int lamp_measure_ex2_rate(double* ex2_per_clk_per_sm);
 
 /* Self-test of failure detection on the GPU: launches one thread that waits, with the
- * bounded mbarrier wait of the tensor-core sweeps limited to `polls` polls (1..2^30), on
- * a barrier that nothing arrives on.  The wait gives up, records LAMP_E_TIMEOUT in a
+ * bounded mbarrier wait of the tensor-core sweeps limited to `polls` polls (1..2^30;
+ * a poll suspends for up to 20 us, and every wait also gives up after 4 s), on a
+ * barrier that nothing arrives on.  The wait gives up, records LAMP_E_TIMEOUT in a
  * device status word and the kernel returns normally; *status receives that word
  * (LAMP_E_TIMEOUT expected).  Returns LAMP_OK, or LAMP_E_INVALID / LAMP_E_NOMEM /
  * LAMP_E_CUDA.  The device stays usable afterwards.  Synchronises. */

@@ -868,7 +868,7 @@ static int objective_values(lamp_ctx* ctx, double* out) {
 static inline int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // the envelope gradient on tensor cores: one fused recompute pass per side (S = x.y^T by
-// MMA, P = 2^v w in the epilogue, P.Y by a second MMA), then a float64 finalize
+// MMA, P = 2^v w in the epilogue, P.Y by a second MMA), then a float-float finalize
 static int grad_tc(lamp_ctx* ctx, float* dx, float* dy) {
   const Consts& k = ctx->k;
   const int64_t n_pad = tc_pad(k.n), m_pad = tc_pad(k.m);

@@ -2,9 +2,13 @@
 // stored-cost sweeps): mbarriers with bounded waits, 2-D tensor (TMA) loads, plain bulk
 // copies and the generic/async proxy fence, as inline PTX for sm_103a.
 //
-// Every wait is bounded: after kWaitLimit polls the waiting thread records
-// LAMP_E_TIMEOUT in the context's status word and sets the CTA's error flag, so that the
-// other roles of the CTA stop issuing work and the kernel returns.
+// Every wait is bounded: after kWaitLimit polls, or kWaitNs nanoseconds of the global
+// timer, the waiting thread records LAMP_E_TIMEOUT in the context's status word and sets
+// the CTA's error flag, so that the other roles of the CTA stop issuing work and the
+// kernel returns.  A poll that finds the phase incomplete suspends the thread for up to
+// kSuspendNs (the try_wait time hint; the thread resumes when the phase completes), so
+// waiting warps (the TMA producer and the MMA issuer, which wait most of the time) take
+// few issue slots from the epilogue warps on their schedulers.
 #pragma once
 
 #include <cuda.h>
@@ -52,13 +56,40 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+constexpr uint32_t kSuspendNs = 20000;       // suspend-time hint of a waiting try_wait
+constexpr uint64_t kWaitNs = 4000000000ull;  // a wait gives up after 4 s
+
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      "selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
+      : "memory");
+  return ok != 0;
+}
+
+// the global timer (nanoseconds)
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
 // bounded wait for the phase of the given parity; false when the CTA's error flag is set
 // or the limit ran out (then the flag and the context status are set)
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, DevState* dev,
                                           uint32_t limit = kWaitLimit) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
   for (uint32_t it = 0; it < limit; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_hint(bar, parity)) return true;
     if (*(volatile int*)err) return false;
+    if (global_ns() - t0 > kWaitNs) break;
   }
   atomicExch(err, 1);
   atomicExch(&dev->status, kTimeoutStatus);

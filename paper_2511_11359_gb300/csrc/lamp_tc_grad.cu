@@ -16,8 +16,9 @@
 //             CTA's whole range of streamed tiles.
 // yT is a transposed bf16 copy of the streamed points (64 coordinates x points), so both
 // MMAs read K-major 128-byte-swizzled tiles written by TMA.  The CTA writes its O rows as
-// float32 partials per inner split; k_tc_grad_fin adds the splits in float64 and forms the
-// gradient.
+// float32 partials per inner split; k_tc_grad_fin adds the splits as a float-float pair and
+// forms the gradient in float-float arithmetic (one float64 conversion per point: this
+// part's FP64 rate is a small fraction of its FP32 rate).
 //
 // CTA = 10 warps: warps 0-7 epilogue (warp w: TMEM lanes 32 (w % 4) .. + 31, i.e. one fixed
 // point per thread, and streamed columns [32 (w / 4), + 32)), warp 8 TMA producer, warp 9
@@ -414,22 +415,48 @@ __global__ void k_transpose_bf16(const __nv_bfloat16* __restrict__ Pb, int64_t n
 }
 
 // dx_i = 2 s (mass_i P_i - wgt_i sum_splits part_i) for rows (mass r_i, wgt q_i) and
-// dy_j = 2 s (A_j P_j - w_j sum_splits part_j) for columns; coordinates q < d
-__global__ void k_tc_grad_fin(const float* __restrict__ part, int splits, int64_t np, int d, const float* __restrict__ P,
-                              const double* __restrict__ mass, const float4* __restrict__ wsrc, double s,
-                              float* __restrict__ out) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= np * d) return;
-  const int64_t i = e / d;
-  const int q = (int)(e - i * d);
+// dy_j = 2 s (A_j P_j - w_j sum_splits part_j) for columns; coordinates q < d.
+// A block of 256 threads takes kFinPoints points x 64 coordinate slots (slots q >= d idle).
+// The two products are formed as float-float pairs (the rounding error of each float32
+// product recovered by an fma, the mass split into float32 high and low parts) and their
+// difference by TwoSum: the two terms nearly cancel where x_i is close to its barycentric
+// image, and the pair keeps ~44 bits of them before the result is rounded to float32.
+constexpr int kFinPoints = 4;
+__global__ void __launch_bounds__(kFinPoints * 64)
+k_tc_grad_fin(const float* __restrict__ part, int splits, int64_t np, int d, const float* __restrict__ P,
+              const double* __restrict__ mass, const float4* __restrict__ wsrc, float s2, float* __restrict__ out) {
+  __shared__ float2 msplit[kFinPoints];
+  const int64_t i0 = (int64_t)blockIdx.x * kFinPoints;
+  if (threadIdx.x < kFinPoints) {
+    const int64_t i = i0 + threadIdx.x;
+    float2 v = make_float2(0.f, 0.f);
+    if (i < np) {
+      const double a = mass[i];
+      const float h = (float)a;
+      v = make_float2(h, (float)(a - (double)h));
+    }
+    msplit[threadIdx.x] = v;
+  }
+  __syncthreads();
+  const int li = threadIdx.x >> 6;
+  const int q = threadIdx.x & 63;
+  const int64_t i = i0 + li;
+  if (i >= np || q >= d) return;
   // the splits' partials are independent loads: issued together (unrolled), added in split
-  // order as a float-float pair (TwoSum), converted once
+  // order as a float-float pair (TwoSum)
   float hi = 0.f, lo = 0.f;
 #pragma unroll 8
   for (int sp = 0; sp < splits; ++sp) ff_add(hi, lo, part[((int64_t)sp * np + i) * kK + q]);
-  const double acc = (double)hi + (double)lo;
-  const double wgt = (double)wsrc[i].y;
-  out[e] = (float)(2.0 * s * (mass[i] * (double)P[e] - wgt * acc));
+  const float2 ms = msplit[li];
+  const float p = P[i * d + q];
+  const float wg = wsrc[i].y;
+  const float t1 = ms.x * p;
+  const float e1 = fmaf(ms.x, p, -t1) + ms.y * p;
+  const float t2 = wg * hi;
+  const float e2 = fmaf(wg, hi, -t2) + wg * lo;
+  float sh, se;
+  two_sum(t1, -t2, sh, se);
+  out[i * d + q] = s2 * (sh + (se + (e1 - e2)));
 }
 
 }  // namespace tcg
@@ -482,9 +509,9 @@ cudaError_t tcg_launch(bool rows, const void* map_fixed, const void* map_stream,
 cudaError_t tcg_finalize(bool rows, const float* part, int splits, const Work& w, const Consts& k, const float* P,
                          const double* r, const float4* wsrc, float* out, cudaStream_t st) {
   const int64_t np = rows ? k.n : k.m;
-  const int64_t total = np * k.d;
-  tcg::k_tc_grad_fin<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(part, splits, np, (int)k.d, P,
-                                                                      rows ? r : w.colA, wsrc, k.s, out);
+  const unsigned blocks = (unsigned)((np + tcg::kFinPoints - 1) / tcg::kFinPoints);
+  tcg::k_tc_grad_fin<<<blocks, tcg::kFinPoints * 64, 0, st>>>(part, splits, np, (int)k.d, P, rows ? r : w.colA,
+                                                              wsrc, (float)(2.0 * k.s), out);
   return cudaGetLastError();
 }
 
