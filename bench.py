@@ -536,6 +536,16 @@ def run_gpu(args, rank, world):
     roof["kernel_ms"] = {"row_sweep": kern_ms[0], "row_fin": kern_ms[1], "col_sweep": kern_ms[2],
                          "col_fin": kern_ms[3]}
     roof["peak_of"] = src
+    if not bytes_per_entry and (args.prec == "bf16_tc" or w.d <= 8):
+        # the whole iteration against the MUFU rate, counting 2 ex2 per entry per iteration
+        # (one per marginal evaluation of Alg. 2, Step 1) and, as built, 4: with O(n + m)
+        # memory each of the two evaluations needs its row normalisers before its column
+        # sums, so every entry is formed once in the row sweep and once in the column sweep
+        it_s = (total_ms / args.steps) / 1e3
+        roof["iteration"] = {
+            "ms": total_ms / args.steps, "peak_Tex2_s": mufu["peak"],
+            "frac_2ex2_per_entry": n * m * 2 / it_s / 1e12 / mufu["peak"],
+            "frac_4ex2_per_entry_as_built": n * m * 4 / it_s / 1e12 / mufu["peak"]}
 
     cpu = None
     if not args.no_cpu_baseline:
