@@ -22,7 +22,11 @@
 //
 // CTA = 10 warps: warps 0-7 epilogue (warp w: TMEM lanes 32 (w % 4) .. + 31, i.e. one fixed
 // point per thread, and streamed columns [32 (w / 4), + 32)), warp 8 TMA producer, warp 9
-// MMA issuer.  TMEM: S double-buffered (2 x 64 columns), O (64), P_hi (32), P_lo (32): 256.
+// MMA issuer.  TMEM: three 64-column buffers, each holding S of a tile and then, written by
+// the epilogue over the S it has read, P_hi and P_lo of that tile (MMA 2's A operand), and
+// O (64 columns): 256.  The epilogue thus never waits for MMA 2: MMA 1 of tile i + 3 waits
+// until MMA 2 of tile i has read its buffer, and the issuer runs MMA 1 two tiles ahead of
+// MMA 2 (S of tile i + 2 is issued before P of tile i is awaited).
 // Every mbarrier wait is bounded; on timeout the kernel records LAMP_E_TIMEOUT, stops
 // issuing, waits (bounded) for its own copies and MMAs, frees its TMEM and returns.
 #include <cuda.h>
@@ -60,19 +64,17 @@ constexpr int kProducerWarp = kEpiWarps;
 constexpr int kMmaWarp = kEpiWarps + 1;
 constexpr int kThreads = (kEpiWarps + 2) * 32;
 constexpr uint32_t kTmemCols = 256;
-constexpr uint32_t kColO = 128;    // O accumulator: 64 FP32 columns
-constexpr uint32_t kColPhi = 192;  // P_hi: 64 bf16 per lane = 32 columns
-constexpr uint32_t kColPlo = 224;  // P_lo
+constexpr int kBufs = 3;          // S / P buffers of 64 columns each
+constexpr uint32_t kColO = kBufs * kStream;  // O accumulator: 64 FP32 columns
 static_assert(kEpiWarps == 8 && kStream == 2 * kSliceCols, "epilogue layout: 4 lane quadrants x 2 slices");
 
 struct __align__(8) Bars {
   uint64_t fixed_full;
   uint64_t full[kStages];   // points tile and transposed tile of a ring slot landed
   uint64_t empty[kStages];  // both MMAs of the slot's tile done
-  uint64_t s_full[2];       // MMA 1 wrote an S buffer
-  uint64_t s_empty[2];      // the epilogue read it
-  uint64_t p_full;          // the epilogue stored P_hi, P_lo
-  uint64_t p_empty;         // MMA 2 read them
+  uint64_t s_full[kBufs];   // MMA 1 wrote S into a buffer
+  uint64_t p_full[kBufs];   // the epilogue replaced it by P_hi, P_lo
+  uint64_t buf_free[kBufs]; // MMA 2 read P: the buffer takes the next S
   uint64_t o_full;          // the last MMA 2 completed: O is final
   uint64_t drain;           // error path: every MMA issued so far completed
   uint64_t pair_full[2];    // packed offsets / weights of a streamed tile landed (bulk copy)
@@ -195,14 +197,15 @@ k_tc_grad(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant__
       mbar_init(&B->full[s], 1);
       mbar_init(&B->empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kBufs; ++b) {
       mbar_init(&B->s_full[b], 1);
-      mbar_init(&B->s_empty[b], kEpiThreads);
+      mbar_init(&B->p_full[b], kEpiThreads);
+      mbar_init(&B->buf_free[b], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
       mbar_init(&B->pair_full[b], 1);
       mbar_init(&B->pair_empty[b], kEpiThreads);
     }
-    mbar_init(&B->p_full, kEpiThreads);
-    mbar_init(&B->p_empty, 1);
     mbar_init(&B->o_full, 1);
     mbar_init(&B->drain, 1);
     B->err = 0;
@@ -253,39 +256,45 @@ k_tc_grad(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant__
       const uint32_t sF = smem_u32(sFixed);
       bool any = false;
       if (mbar_wait(&B->fixed_full, 0, B, dev)) {
-        for (int i = 0; i <= ntiles; ++i) {
-          if (i < ntiles) {
-            // MMA 1 of tile i: S[b] = x_fixed . stream_i^T
-            const int s = i % kStages;
-            const int b = i & 1;
-            if (!mbar_wait(&B->full[s], (i / kStages) & 1, B, dev)) break;
-            if (i >= 2 && !mbar_wait(&B->s_empty[b], ((i >> 1) - 1) & 1, B, dev)) break;
-            tc_fence_after();
-            const uint32_t sS = smem_u32(sStream + s * kStreamBytes);
+        // MMA 1 of tile i into buffer i % kBufs: S = x_fixed . stream_i^T; it runs two tiles
+        // ahead of MMA 2, so S of the tile after next is ready while the epilogue works
+        auto mma1 = [&](int i) -> bool {
+          const int s = i % kStages;
+          const int b = i % kBufs;
+          if (!mbar_wait(&B->full[s], (i / kStages) & 1, B, dev)) return false;
+          if (i >= kBufs && !mbar_wait(&B->buf_free[b], ((i / kBufs) - 1) & 1, B, dev)) return false;
+          tc_fence_after();
+          const uint32_t sS = smem_u32(sStream + s * kStreamBytes);
 #pragma unroll
-            for (int kk = 0; kk < kK / 16; ++kk)
-              umma_bf16(tmem + b * kStream, sdesc_sw128(sF + kk * 32), sdesc_sw128(sS + kk * 32), idesc, kk > 0);
-            umma_commit(&B->s_full[b]);
-            any = true;
-          }
-          if (i >= 1) {
-            // MMA 2 of tile j = i - 1: O += P_hi . streamT_j^T + P_lo . streamT_j^T
-            const int j = i - 1;
-            const int sj = j % kStages;
-            if (!mbar_wait(&B->p_full, j & 1, B, dev)) break;
-            tc_fence_after();
-            const uint32_t sT = smem_u32(sStreamT + sj * kStreamBytes);
+          for (int kk = 0; kk < kK / 16; ++kk)
+            umma_bf16(tmem + b * kStream, sdesc_sw128(sF + kk * 32), sdesc_sw128(sS + kk * 32), idesc, kk > 0);
+          umma_commit(&B->s_full[b]);
+          any = true;
+          return true;
+        };
+        bool go = mma1(0) && (ntiles < 2 || mma1(1));
+        for (int j = 0; go && j < ntiles; ++j) {
+          if (j + 2 < ntiles && !mma1(j + 2)) break;
+          // MMA 2 of tile j: O += P_hi . streamT_j^T + P_lo . streamT_j^T
+          const int sj = j % kStages;
+          const int bj = j % kBufs;
+          if (!mbar_wait(&B->p_full[bj], (j / kBufs) & 1, B, dev)) break;
+          tc_fence_after();
+          const uint32_t sT = smem_u32(sStreamT + sj * kStreamBytes);
+          // P of streamed points [16 kk, 16 kk + 16): slice kk / 2, half kk % 2 of the buffer
+          // (8 columns of P_hi, then 8 of P_lo)
+          const uint32_t pb = tmem + bj * kStream;
 #pragma unroll
-            for (int kk = 0; kk < kStream / 16; ++kk)
-              umma_bf16_ts(tmem + kColO, tmem + kColPhi + kk * 8, sdesc_sw128(sT + kk * 32), idesc,
-                           (j > 0 || kk > 0) ? 1u : 0u);
+          for (int kk = 0; kk < kStream / 16; ++kk)
+            umma_bf16_ts(tmem + kColO, pb + (kk >> 1) * kSliceCols + (kk & 1) * 16, sdesc_sw128(sT + kk * 32),
+                         idesc, (j > 0 || kk > 0) ? 1u : 0u);
 #pragma unroll
-            for (int kk = 0; kk < kStream / 16; ++kk)
-              umma_bf16_ts(tmem + kColO, tmem + kColPlo + kk * 8, sdesc_sw128(sT + kk * 32), idesc, 1u);
-            umma_commit(&B->p_empty);
-            umma_commit(&B->empty[sj]);
-            if (j == ntiles - 1) umma_commit(&B->o_full);
-          }
+          for (int kk = 0; kk < kStream / 16; ++kk)
+            umma_bf16_ts(tmem + kColO, pb + (kk >> 1) * kSliceCols + (kk & 1) * 16 + 8, sdesc_sw128(sT + kk * 32),
+                         idesc, 1u);
+          umma_commit(&B->buf_free[bj]);
+          umma_commit(&B->empty[sj]);
+          if (j == ntiles - 1) umma_commit(&B->o_full);
         }
       }
       if (*(volatile int*)&B->err && any) {
@@ -312,19 +321,20 @@ k_tc_grad(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant__
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     bool ok = true;
     for (int i = 0; i < ntiles; ++i) {
-      const int b = i & 1;
+      const int b = i & 1;       // packed-pair buffer
+      const int sb = i % kBufs;  // S / P buffer
       ok = mbar_wait(&B->pair_full[b], (i >> 1) & 1, B, dev);
-      ok = ok && mbar_wait(&B->s_full[b], (i >> 1) & 1, B, dev);
+      ok = ok && mbar_wait(&B->s_full[sb], (i / kBufs) & 1, B, dev);
       if (!__all_sync(0xffffffffu, ok)) {
         ok = false;
         break;
       }
       tc_fence_after();
       const float4* pr = sPair + (size_t)b * kStream;
-      const uint32_t tbase = tmem + lane_base + b * kStream + h * kSliceCols;
-      // two halves of 16 columns: P of the first half is stored once the previous tile's MMA 2
-      // has read P (by then long done), so no wait stalls the start of a tile, and only 8
-      // words of each part are held in registers
+      const uint32_t tbase = tmem + lane_base + sb * kStream + h * kSliceCols;
+      // two halves of 16 columns; P of a half replaces the S columns of that half (P_hi in
+      // the first 8, P_lo in the next 8), which this thread has already read: every thread
+      // writes only its own lane of its own slice, so no other thread's S is overwritten
       uint32_t vv[2][8];
       tmem_ld8(tbase, vv[0]);
       tmem_wait_ld8(vv[0]);
@@ -351,26 +361,14 @@ k_tc_grad(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant__
           }
           if (c + 1 < kSliceCols / 8) tmem_wait_ld8(vv[(c + 1) & 1]);
         }
-        if (half == 0) {
-          // P of the previous tile has been consumed by its MMA 2 before it is overwritten
-          ok = i == 0 || mbar_wait(&B->p_empty, (i - 1) & 1, B, dev);
-          if (!__all_sync(0xffffffffu, ok)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-        }
-        tmem_st8(tmem + lane_base + kColPhi + h * (kSliceCols / 2) + half * 8, phi);
-        tmem_st8(tmem + lane_base + kColPlo + h * (kSliceCols / 2) + half * 8, plo);
+        tmem_st8(tbase + half * 16, phi);
+        tmem_st8(tbase + half * 16 + 8, plo);
       }
-      if (!ok) break;
-      tc_fence_before();
-      mbar_arrive(&B->s_empty[b]);
       fence_proxy_async_smem();  // the pair buffer was read through the generic proxy
       mbar_arrive(&B->pair_empty[b]);
       tmem_wait_st();
       tc_fence_before();
-      mbar_arrive(&B->p_full);
+      mbar_arrive(&B->p_full[sb]);
     }
     // O rows of this CTA's split: coordinates [32 h, 32 h + 32) of the fixed point t
     float o[32];
