@@ -221,6 +221,24 @@ __device__ __forceinline__ float4 column_data(double nu_j, double nubar_j, doubl
   return make_float4((float)qA, exp2f((float)(qA - bA)), (float)qB, exp2f((float)(qB - bB)));
 }
 
+// Visit the per-split partials of one point in split order: ld(s) loads split s's values,
+// use(v) consumes them.  The loads are issued in groups of 8 before any of them is used: a
+// loop over a run-time number of splits below its unroll factor would otherwise issue one
+// load per trip, each behind the add of the previous one.
+template <typename LD, typename USE>
+__device__ __forceinline__ void for_splits(int splits, LD&& ld, USE&& use) {
+  using V = decltype(ld(0));
+  for (int s0 = 0; s0 < splits; s0 += 8) {
+    V v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (s0 + u < splits) v[u] = ld(s0 + u);
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (s0 + u < splits) use(v[u]);
+  }
+}
+
 // Knuth's branch-free TwoSum: s + e == a + b exactly
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;

@@ -425,29 +425,34 @@ k_tc_grad_fin(const float* __restrict__ part, int splits, int64_t np, int d, con
               const double* __restrict__ mass, const float4* __restrict__ wsrc, float s2, float* __restrict__ out) {
   __shared__ float2 msplit[kFinPoints];
   const int64_t i0 = (int64_t)blockIdx.x * kFinPoints;
+  const int li = threadIdx.x >> 6;
+  const int q = threadIdx.x & 63;
+  const int64_t i = i0 + li;
+  const bool act = i < np && q < d;
+  // every load is issued before the block barrier, so that the mass loads of the first
+  // threads and the partials of all threads are in flight together
+  double a = 0.0;
+  const bool splitter = threadIdx.x < kFinPoints && i0 + threadIdx.x < np;
+  if (splitter) a = mass[i0 + threadIdx.x];
+  // the splits' partials, added in split order as a float-float pair (TwoSum)
+  float hi = 0.f, lo = 0.f, p = 0.f, wg = 0.f;
+  if (act) {
+    p = P[i * d + q];
+    wg = wsrc[i].y;
+    for_splits(
+        splits, [&](int sp) { return part[((int64_t)sp * np + i) * kK + q]; }, [&](float v) { ff_add(hi, lo, v); });
+  }
   if (threadIdx.x < kFinPoints) {
-    const int64_t i = i0 + threadIdx.x;
     float2 v = make_float2(0.f, 0.f);
-    if (i < np) {
-      const double a = mass[i];
+    if (splitter) {
       const float h = (float)a;
       v = make_float2(h, (float)(a - (double)h));
     }
     msplit[threadIdx.x] = v;
   }
   __syncthreads();
-  const int li = threadIdx.x >> 6;
-  const int q = threadIdx.x & 63;
-  const int64_t i = i0 + li;
-  if (i >= np || q >= d) return;
-  // the splits' partials are independent loads: issued together (unrolled), added in split
-  // order as a float-float pair (TwoSum)
-  float hi = 0.f, lo = 0.f;
-#pragma unroll 8
-  for (int sp = 0; sp < splits; ++sp) ff_add(hi, lo, part[((int64_t)sp * np + i) * kK + q]);
+  if (!act) return;
   const float2 ms = msplit[li];
-  const float p = P[i * d + q];
-  const float wg = wsrc[i].y;
   const float t1 = ms.x * p;
   const float e1 = fmaf(ms.x, p, -t1) + ms.y * p;
   const float t2 = wg * hi;
