@@ -443,6 +443,19 @@ def run_gpu(args, rank, world):
         info["cost_at_tol"] = s2.objective()["cost"]
         s2_state = s2.get_state()
         s2.close()
+        if w.eta > 0:
+            # for eta > 0 the rule above also waits for 1 - kappa_t eta <= tol; the same solve
+            # stopped by the infeasibility alone (lamp_params.infeas_only)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p3 = dict(params, infeas_only=1)
+            s3 = L.Lamp(r, c, x=x, y=y, cost_scale=w.cost_scale, max_iter=args.ttt_max_iter,
+                        **p3) if w.kind != "dense" else L.Lamp(r, c, C=C, max_iter=args.ttt_max_iter, **p3)
+            r3 = s3.solve()
+            info["time_to_tol_infeas_only"] = {"seconds": time.perf_counter() - t0, "iters": r3["iters"],
+                                               "infeas": r3["infeas"], "converged": r3["converged"],
+                                               "tol": w.tol, "cost": s3.objective()["cost"]}
+            s3.close()
         if w.kind != "dense":
             # the autograd form: lamp_ot_loss forward (context creation, solve to tol, objective)
             # and the hand-written backward (lamp_grad)
