@@ -58,7 +58,7 @@ NCU_TRAFFIC = {
     ("highdim", "bf16_tc", 32768, 64): {
         "source": "paper_2511_11359_gb300/csrc/lamp_tc.cu",
         "sha256": "ee6853d9906ab7d1f537ad7309f51ccfb5021d5897ef979de59d0544ed4f722c",
-        "row_sweep": 9223680, "col_sweep": 10012928},
+        "row_sweep": 9203456, "col_sweep": 9990144},
     ("image_grid", "fp32", 4096, 0): {
         "source": "paper_2511_11359_gb300/csrc/lamp_dense.cu",
         "sha256": "0214d7ff91ff3f635ac75b39f297454933f9a9a9becf2116f747fecebaf78424",
