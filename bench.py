@@ -52,33 +52,42 @@ def job_throughput(units_per_rank: float, local_seconds: float, dist=None, devic
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the sweeps from one
 # ncu capture of this bench's own command line, keyed by (workload, prec, n, d).  A figure is
-# reported only while the kernel source it was taken on is unchanged (sha256 of that file):
-# after any edit of the kernel the counters no longer describe it and `traffic` is null.
+# reported only while the kernel's sources are those it was taken on (sha256 over the files
+# that make up the kernel): after any edit of them the counters no longer describe it and
+# `traffic` is null.
 NCU_TRAFFIC = {
     ("highdim", "bf16_tc", 32768, 64): {
-        "source": "paper_2511_11359_gb300/csrc/lamp_tc.cu",
-        "sha256": "ee6853d9906ab7d1f537ad7309f51ccfb5021d5897ef979de59d0544ed4f722c",
+        "sources": ["paper_2511_11359_gb300/csrc/lamp_tc.cu", "paper_2511_11359_gb300/csrc/lamp_tc.cuh",
+                    "paper_2511_11359_gb300/csrc/lamp_async.cuh", "paper_2511_11359_gb300/csrc/lamp_common.cuh"],
+        "sha256": "37168869558cd64514d6095e3ff15883b365f706c0a1e35b09eee692d4d2ed03",
         "row_sweep": 9203456, "col_sweep": 9990144},
     ("image_grid", "fp32", 4096, 0): {
-        "source": "paper_2511_11359_gb300/csrc/lamp_dense.cu",
-        "sha256": "0214d7ff91ff3f635ac75b39f297454933f9a9a9becf2116f747fecebaf78424",
-        "row_sweep": 67254016 + 217088, "col_sweep": 67259648 + 328960},
+        "sources": ["paper_2511_11359_gb300/csrc/lamp_dense.cu", "paper_2511_11359_gb300/csrc/lamp_async.cuh",
+                    "paper_2511_11359_gb300/csrc/lamp_common.cuh"],
+        "sha256": "61d2c461514d13861b82ae999b5ce9986d3999b359c1fba50280d88da1925b2a",
+        "row_sweep": 67246848 + 244224, "col_sweep": 67254016 + 358912},
 }
 
 
-def ncu_traffic(workload, prec, n, d, which):
+def sources_digest(sources):
+    """sha256 over the concatenated bytes of the given repo files (None if one is missing)."""
     import hashlib
 
+    h = hashlib.sha256()
+    for rel in sources:
+        try:
+            with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), rel), "rb") as f:
+                h.update(f.read())
+        except OSError:
+            return None
+    return h.hexdigest()
+
+
+def ncu_traffic(workload, prec, n, d, which):
     rec = NCU_TRAFFIC.get((workload, prec, n, d))
     if rec is None:
         return None
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), rec["source"])
-    try:
-        with open(path, "rb") as f:
-            digest = hashlib.sha256(f.read()).hexdigest()
-    except OSError:
-        return None
-    return rec[which] if digest == rec["sha256"] else None
+    return rec[which] if sources_digest(rec["sources"]) == rec["sha256"] else None
 
 
 def load_peaks():
@@ -528,10 +537,10 @@ def run_gpu(args, rank, world):
             roof = dict(mufu)
         else:
             # the FP32 pipe binds the direct form: float32 lane operations per entry of a regular
-            # iteration: d sub + d mul/fma (cost); stream A add + 2 fma (compensated exponent) +
+            # iteration: d sub + d mul/fma (cost); stream A add + fma (compensated exponent) +
             # fma (weighted sum); stream B, through the shared row shift, add + fma + fma; at d = 3
-            # that is 13 lane-ops, 9.8 entries / clk / SM, against 16 for MUFU
-            lanes = 2 * w.d + 7
+            # that is 12 lane-ops, 10.7 entries / clk / SM, against 16 for MUFU
+            lanes = 2 * w.d + 6
             fpeak = sms * 128 * mhz * 1e6 / 1e12
             fach = n * m * lanes / (kern_ms[dom] / 1e3) / 1e12
             roof = {"bound": "alu", "achieved": fach, "peak": fpeak, "unit": "Tlane-op/s", "frac": fach / fpeak,

@@ -14,14 +14,20 @@ import bench  # noqa: E402
 
 def test_traffic_is_reported_for_the_captured_source_only(monkeypatch, tmp_path):
     src = tmp_path / "kernel.cu"
+    hdr = tmp_path / "kernel.cuh"
     src.write_text("__global__ void k() {}\n")
-    digest = hashlib.sha256(src.read_bytes()).hexdigest()
-    rel = os.path.relpath(src, ROOT)
+    hdr.write_text("#pragma once\n")
+    digest = hashlib.sha256(src.read_bytes() + hdr.read_bytes()).hexdigest()
+    rels = [os.path.relpath(src, ROOT), os.path.relpath(hdr, ROOT)]
     monkeypatch.setattr(bench, "NCU_TRAFFIC", {
-        ("w", "p", 8, 2): {"source": rel, "sha256": digest, "row_sweep": 111, "col_sweep": 222}})
+        ("w", "p", 8, 2): {"sources": rels, "sha256": digest, "row_sweep": 111, "col_sweep": 222}})
     assert bench.ncu_traffic("w", "p", 8, 2, "row_sweep") == 111
     assert bench.ncu_traffic("w", "p", 8, 2, "col_sweep") == 222
     assert bench.ncu_traffic("w", "p", 16, 2, "row_sweep") is None  # another size
+    hdr.write_text("#pragma once\n// changed\n")
+    assert bench.ncu_traffic("w", "p", 8, 2, "row_sweep") is None  # a header of the kernel changed
+    hdr.write_text("#pragma once\n")
+    assert bench.ncu_traffic("w", "p", 8, 2, "row_sweep") == 111
     src.write_text("__global__ void k() { /* changed */ }\n")
     assert bench.ncu_traffic("w", "p", 8, 2, "row_sweep") is None  # the kernel changed
 
@@ -30,10 +36,13 @@ def test_recorded_traffic_matches_the_committed_sources():
     """Every committed record names an existing source, and a record whose hash no longer
     matches its source reports null rather than a stale figure."""
     for key, rec in bench.NCU_TRAFFIC.items():
-        path = os.path.join(ROOT, rec["source"])
-        assert os.path.exists(path), key
-        with open(path, "rb") as f:
-            current = hashlib.sha256(f.read()).hexdigest()
+        h = hashlib.sha256()
+        for rel in rec["sources"]:
+            path = os.path.join(ROOT, rel)
+            assert os.path.exists(path), key
+            with open(path, "rb") as f:
+                h.update(f.read())
+        current = h.hexdigest()
         value = bench.ncu_traffic(*key, "row_sweep")
         assert (value is not None) == (current == rec["sha256"]), key
 
