@@ -388,3 +388,27 @@ def test_host_buffer_entry_point():
     O.lamp_run(C, w.r, w.c, O.LampParams(K=K), 30, record=lambda st, i: rec.append(i.res))
     assert inf == pytest.approx(rec[-1], rel=1e-5)
     h.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16_tc"])
+def test_host_buffer_steps_repeat_the_device_context(prec):
+    """lamp_step_host re-uploads the host inputs (and re-converts them to bf16 for the
+    tensor-core path) before each step: three steps of 4 iterations give bit for bit the
+    state of a context on device inputs after 12 iterations."""
+    import torch
+    import paper_2511_11359_gb300 as L
+
+    w = W.highdim(n=700, m=650, d=16, seed=9)
+    h = L.LampHost(w.r, w.c, x=w.x, y=w.y, prec=prec, check_every=4)
+    nu = np.empty(650)
+    for _ in range(3):
+        inf = h.step(4, nu_out=nu)
+    h.close()
+    dev = torch.device("cuda", 0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    s = L.Lamp(t(w.r), t(w.c), x=t(w.x), y=t(w.y), prec=prec, check_every=4)
+    s.iterate(12)
+    st = s.get_state()
+    s.close()
+    assert np.array_equal(nu, st["nu"])
+    assert math.isfinite(inf) and inf > 0.0
