@@ -365,9 +365,14 @@ static int create_impl(lamp_ctx** out, const lamp_problem* prob, const lamp_para
     const auto mi = [&](int64_t tout, int64_t tin, int64_t wave, int base) {
       return tout * std::max<int64_t>(tin / base, 1) * 4 < wave ? 1 : base;
     };
-    g.rows_split = choose_split(to, ti, (int64_t)g.sms * bpr, mi(to, ti, (int64_t)g.sms * bpr, min_inner));
+    // a split costs 0.2 % of a wave in the score (0.06 % for the tensor-core sweeps, whose
+    // CTAs carry little fixed cost: at n = m = 2^15 19 splits, exactly 8 waves of 304 CTAs,
+    // beat 7 splits, 2.95 waves, by 1.4 % per iteration including the finalizes' longer sums)
+    const double per_split = tcp ? 0.0006 : 0.002;
+    g.rows_split = choose_split(to, ti, (int64_t)g.sms * bpr, mi(to, ti, (int64_t)g.sms * bpr, min_inner), per_split);
     g.cols_split = choose_split(tco, tci, (int64_t)g.sms * bpc,
-                                mi(tco, tci, (int64_t)g.sms * bpc, k.kind == LAMP_COST_DENSE ? 4 : min_inner));
+                                mi(tco, tci, (int64_t)g.sms * bpc, k.kind == LAMP_COST_DENSE ? 4 : min_inner),
+                                per_split);
     if (k.kind == LAMP_COST_DENSE && dense_make_map(ctx->map_c, in.C, k.n, k.m, in.ldc) == cudaSuccess &&
         dense_prepare() == cudaSuccess) {
       // a stored cost with a 16-byte aligned base and rows a multiple of 16 bytes apart:

@@ -123,7 +123,7 @@ k_pts_direct(const float* __restrict__ P_out, const float* __restrict__ P_in, in
   }
 
   const SweepF sp = sweep_floats_of(dev, k);
-  const uint64_t ahA2 = pk(sp.ahA, sp.ahA);
+  const uint64_t ahA2 = pk(sp.ahA, sp.ahA), alA2 = pk(sp.alA, sp.alA);
   const float dal = sp.dal;  // a^B - a^A
   const uint64_t da2 = pk(dal, dal);
 
@@ -204,10 +204,7 @@ k_pts_direct(const float* __restrict__ P_out, const float* __restrict__ P_in, in
               z2 = CK == 1 ? f2add(z2, ad) : f2max(z2, ad);
             }
           }
-          // v^A = a^A z + own + off with a^A rounded to float32 (ah): the low part al z is at
-          // most half an ulp of a^A z, the order of the float32 rounding of z itself (a
-          // relative change of kappa by 2^-24); the tensor-core sweeps evaluate the same form
-          const uint64_t vA = f2fma(ahA2, z2, f2add(ownA[r], oA2));
+          const uint64_t vA = f2fma(alA2, z2, f2fma(ahA2, z2, f2add(ownA[r], oA2)));
           const uint64_t vB = f2fma(da2, z2, f2add(vA, MODE == M_ROWSUM ? dC2 : ownD[r]));
           const float2 vAf = upk(vA), vBf = upk(vB);
           const uint64_t eA = pk(ex2(vAf.x), ex2(vAf.y));

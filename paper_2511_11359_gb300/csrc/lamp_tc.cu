@@ -259,8 +259,7 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
     const SweepF sp = sweep_floats_of(dev, k);
     // v^A = a^A z + own + off with a^A rounded to float32 (ah): dropping the low part al
     // changes v by at most half an ulp of a^A z, the order of the rounding of z itself in
-    // the MMA's FP32 accumulation (the packed direct-form sweeps drop it too; the float32
-    // dot form and the stored-cost sweeps keep al)
+    // the MMA's FP32 accumulation (the float32 CUDA-core paths keep al)
     const uint64_t ahA2 = pk(sp.ahA, sp.ahA);
     const float dal = sp.dal;  // stream B: v^B = (a^B - a^A) z + (v^A + dB)
     const uint64_t da2 = pk(dal, dal);
