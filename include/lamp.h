@@ -244,7 +244,9 @@ LAMP_API int lamp_round(lamp_ctx* ctx, double out[4], double* y, double* delta_r
  *   epilogue and split into two bf16 parts (16 significant bits), sum_j X_ij y_j by a
  *   second tcgen05 MMA with float32 accumulation; the first call allocates transposed
  *   bf16 copies of the points (O((n + m) 64)) and float32 partial sums (O((n + m) 64)
- *   per inner split).
+ *   per inner split), and a second stream of its own: with both dx and dy requested the
+ *   dy side runs on it, forked from and joined back into the context's stream, so work
+ *   queued later on the context's stream sees both results.
  * SQEUCLID only (LAMP_E_UNSUPPORTED otherwise).  Asynchronous. */
 LAMP_API int lamp_grad(lamp_ctx* ctx, float* dx, float* dy);
 

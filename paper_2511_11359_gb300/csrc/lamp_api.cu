@@ -62,6 +62,8 @@ struct lamp_ctx {
   bool tcg_fresh = false;  // the transposed copies match the current bf16 points
   float* tcg_part = nullptr;
   size_t tcg_part_floats = 0;
+  cudaStream_t gside = nullptr;  // the gradient's second side runs on this stream
+  cudaEvent_t gfork = nullptr, gjoin = nullptr;
   alignas(64) unsigned char map_xT[128];
   alignas(64) unsigned char map_yT[128];
   std::string err;
@@ -891,7 +893,16 @@ static int grad_tc(lamp_ctx* ctx, float* dx, float* dy) {
     CK(tc_make_map2(ctx->map_yT, ctx->yT, m_pad, 64, 64, 64));
     ctx->tcg_fresh = false;
   }
-  const size_t need = (size_t)std::max<int64_t>((int64_t)sx * k.n, (int64_t)sy * k.m) * 64;
+  // the two sides run concurrently (dx on the context's stream, dy on a side stream), each
+  // with partials of its own: one side's tail overlaps the other side's start
+  const size_t need_x = (size_t)sx * k.n * 64, need_y = (size_t)sy * k.m * 64;
+  const size_t need = need_x + need_y;
+  if (!ctx->gside) {
+    if (cudaStreamCreateWithFlags(&ctx->gside, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->gfork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->gjoin, cudaEventDisableTiming) != cudaSuccess)
+      return fail(ctx, LAMP_E_CUDA, "lamp_grad: stream / event creation failed");
+  }
   if (need > ctx->tcg_part_floats) {
     if (ctx->tcg_part) {
       CK(cudaStreamSynchronize(ctx->stream));
@@ -911,13 +922,23 @@ static int grad_tc(lamp_ctx* ctx, float* dx, float* dy) {
   }
   if ((rc = evaluate_if_stale(ctx))) return rc;
   const int cur = ctx->host_dev->cur;
+  cudaStream_t sy_st = dx ? ctx->gside : ctx->stream;
+  if (dx && dy) {
+    CK(cudaEventRecord(ctx->gfork, ctx->stream));
+    CK(cudaStreamWaitEvent(sy_st, ctx->gfork, 0));
+  }
   if (dx) {
     CK(tcg_launch(true, ctx->map_x, ctx->map_y64, ctx->map_yT, ctx->w, k, sx, ctx->tcg_part, ctx->stream));
     CK(tcg_finalize(true, ctx->tcg_part, sx, ctx->w, k, ctx->in.x, ctx->in.r, ctx->w.g2row, dx, ctx->stream));
   }
   if (dy) {
-    CK(tcg_launch(false, ctx->map_y, ctx->map_x64, ctx->map_xT, ctx->w, k, sy, ctx->tcg_part, ctx->stream));
-    CK(tcg_finalize(false, ctx->tcg_part, sy, ctx->w, k, ctx->in.y, ctx->in.r, ctx->w.colq[cur], dy, ctx->stream));
+    float* party = ctx->tcg_part + need_x;
+    CK(tcg_launch(false, ctx->map_y, ctx->map_x64, ctx->map_xT, ctx->w, k, sy, party, sy_st));
+    CK(tcg_finalize(false, party, sy, ctx->w, k, ctx->in.y, ctx->in.r, ctx->w.colq[cur], dy, sy_st));
+  }
+  if (dx && dy) {
+    CK(cudaEventRecord(ctx->gjoin, sy_st));
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->gjoin, 0));
   }
   return LAMP_OK;
 }
@@ -1104,5 +1125,11 @@ extern "C" void lamp_destroy(lamp_ctx* ctx) {
   for (void* p : ctx->allocs) cudaFree(p);
   if (ctx->host_dev) cudaFreeHost(ctx->host_dev);
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
+  if (ctx->gside) {
+    cudaStreamSynchronize(ctx->gside);
+    cudaStreamDestroy(ctx->gside);
+  }
+  if (ctx->gfork) cudaEventDestroy(ctx->gfork);
+  if (ctx->gjoin) cudaEventDestroy(ctx->gjoin);
   delete ctx;
 }
