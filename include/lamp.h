@@ -215,7 +215,9 @@ LAMP_API int lamp_apply_map(lamp_ctx* ctx, const float* V, int64_t k, float* out
  * (weak duality).  eta = 0: two row-max sweeps per phi at a large kappa, the second with
  * the row shifts of the first and the sub-grid remainders of the column offsets
  * subtracted, so the row minima of the kernels' float32 cost come out to about 1e-12 K
- * (the float32 cost itself differs from an exact one by its own rounding); eta > 0: a
+ * (the float32 cost itself differs from an exact one by its own rounding; a
+ * LAMP_PREC_BF16_TC context runs both sweeps on the tensor cores, so its bound is on the
+ * cost its iteration uses, x.y of the bf16 points accumulated in float32); eta > 0: a
  * row-max and a row-sum sweep per phi at kappa = 1/eta (relative error of the row sums
  * about 2^-22, i.e. about 2^-22 eta in the softmin).  The state is not changed. */
 LAMP_API int lamp_dual(lamp_ctx* ctx, double out[2]);

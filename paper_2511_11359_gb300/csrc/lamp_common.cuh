@@ -407,7 +407,7 @@ cudaError_t launch_prime(const Inputs& in, const Consts& k, const Work& w, const
                          cudaStream_t st);
 // after launch_prime: per row and split, max_j (v_ij - Br_j) with the primed row shifts
 // applied (Work::rowmax, stream A slot); the column data's second field holds Br_j
-cudaError_t launch_rowmax_refined(const Inputs& in, const Consts& k, const Work& w, const Geometry& g,
+cudaError_t launch_rowmax_refined(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
                                   cudaStream_t st);
 // eval = 1: an evaluation pass, whose column sweep also accumulates <C, X^t> (the
 // packed direct-form column sweep leaves it out of the regular iterations)
@@ -452,6 +452,7 @@ int tc_blocks_per_sm(int which);
 // eval = 1: the column sweep of an evaluation pass (with the cost-weighted sums)
 cudaError_t tc_launch_sweep(bool rows, int eval, const Geometry& g, const Work& w, const Consts& k, int splits,
                             cudaStream_t st);
+cudaError_t tc_launch_rowmax(int mode, const Geometry& g, const Work& w, const Consts& k, int splits, cudaStream_t st);
 cudaError_t launch_iteration_part(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
                                   int part, int eval, cudaStream_t st);
 int tile_outer_cols(const Consts& k, int prec);

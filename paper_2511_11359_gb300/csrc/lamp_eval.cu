@@ -239,6 +239,8 @@ k_dual_cols(const Work w, int cur, int which, const double* __restrict__ c, floa
       const double b = sp.lamA * (sny + 2.0 * k.K * phi);
       const double q = quantize(b, sp.g);
       colq_s[j] = make_float4((float)q, (float)(b - q), (float)q, (float)(b - q));
+      // the same in the packed-pair layout, which the tensor-core row-max passes read
+      if (colq2_s) store_pair_entry(colq2_s, j, (float)q, (float)(b - q), 0.f, (float)(b - q));
     }
     v = c[j] * phi;
   }
@@ -357,7 +359,7 @@ cudaError_t launch_dual(const Inputs& in, const Consts& k, const Work& w, const 
     // steps, so its float32 rounding (and that of the remainder) is ~2^-24 g, and the row
     // minimum min_j (C_ij + 2K phi_j) of the kernels' cost comes out with an absolute error
     // of order 2^-46 W instead of W 2^-24 (W the offset bound, a few K)
-    e = launch_rowmax_refined(in, k2, w2, g, st);
+    e = launch_rowmax_refined(in, k2, w2, g, prec, st);
     if (e != cudaSuccess) return e;
   }
   k_dual_rows<<<(unsigned)rb, kT, 0, st>>>(w, w.rowshift[nx], g.rows_split, in.r, soft ? 1 : 0, rowp, k2);

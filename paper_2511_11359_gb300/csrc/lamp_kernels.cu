@@ -1065,14 +1065,18 @@ static cudaError_t launch_col_sweep(const Inputs& in, const Consts& k, const Wor
 
 cudaError_t launch_prime(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
                          cudaStream_t st) {
-  cudaError_t e = launch_row_sweep(in, k, w, g, M_MAX, st);
+  // the tensor-core context takes its row maxima from the tensor-core sweep (the cost its
+  // iteration uses)
+  cudaError_t e = prec == 1 /* LAMP_PREC_BF16_TC */ && g.map_x ? tc_launch_rowmax(1, g, w, k, g.rows_split, st)
+                                                                : launch_row_sweep(in, k, w, g, M_MAX, st);
   if (e != cudaSuccess) return e;
   k_prime_fin<<<(unsigned)cdiv(k.n, 256), 256, 0, st>>>(w, g.rows_split, k);
   return cudaGetLastError();
 }
 
-cudaError_t launch_rowmax_refined(const Inputs& in, const Consts& k, const Work& w, const Geometry& g,
+cudaError_t launch_rowmax_refined(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
                                   cudaStream_t st) {
+  if (prec == 1 /* LAMP_PREC_BF16_TC */ && g.map_x) return tc_launch_rowmax(2, g, w, k, g.rows_split, st);
   return launch_row_sweep(in, k, w, g, M_MAX2, st);
 }
 

@@ -139,7 +139,12 @@ __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"
 // ROWS = false: G2 (fixed y tile, streamed x tiles, per-column sums of both streams)
 // WC: column sweep of an evaluation pass (also accumulates sum_i z_ij X_ij for <C, X^t>)
 // map_fixed: 128-row boxes of the fixed operand; map_stream: 64-row boxes of the streamed one
-template <bool ROWS, int WC>
+// MODE (row sweeps only): kSums, the iteration's sums; kMax, the row maxima of stream A's
+// exponent without row shift, a z_ij - Bq_j (the prime pass that sets the row shifts);
+// kMax2, the refined row maxima u_ij = a z_ij - (Rq_i + Bq_j) - Br_j with the multiplier's
+// low part (the eta = 0 dual bound's second pass).  The maxima go to rowmax per split.
+constexpr int kSums = 0, kMax = 1, kMax2 = 2;
+template <bool ROWS, int WC, int MODE = kSums>
 __global__ void __launch_bounds__(kThreads, 2)
 k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant__ CUtensorMap map_stream,
            const Work w, int64_t n, int64_t m, int tiles_per_split, const Consts k) {
@@ -261,6 +266,7 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
     // changes v by at most half an ulp of a^A z, the order of the rounding of z itself in
     // the MMA's FP32 accumulation (the float32 CUDA-core paths keep al)
     const uint64_t ahA2 = pk(sp.ahA, sp.ahA);
+    const uint64_t alA2 = pk(sp.alA, sp.alA);  // kMax2 only
     const float dal = sp.dal;  // stream B: v^B = (a^B - a^A) z + (v^A + dB)
     const uint64_t da2 = pk(dal, dal);
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;  // TMEM lane field
@@ -274,7 +280,8 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
       own[r] = fixed0 + r * kTile + t;
       if (ROWS) {
         const float2 rq = w.rowshift[cur][own[r] < n ? own[r] : n - 1];
-        ownA2[r] = pk(-rq.x, -rq.x);
+        const float o = MODE == kMax ? 0.f : -rq.x;  // the prime pass has no row shift yet
+        ownA2[r] = pk(o, o);
       } else {
         const int64_t mp = (m + kPad - 1) / kPad * kPad;  // the column data are padded to mp
         const int64_t oc = own[r] < mp ? own[r] : mp - 1;
@@ -286,6 +293,7 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
     }
     float hiA[2] = {0.f, 0.f}, loA[2] = {0.f, 0.f}, hiB[2] = {0.f, 0.f}, loB[2] = {0.f, 0.f};
     float hiC[2] = {0.f, 0.f}, loC[2] = {0.f, 0.f};
+    float mxA[2] = {-INFINITY, -INFINITY};  // kMax, kMax2: running row maxima
     // packed pair sums of this thread's two points over one streamed tile
     uint64_t accA[2], accB[2], accC[2];
     uint32_t vv[2][16];  // two TMEM chunks: the one evaluated and the one in flight
@@ -314,6 +322,18 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
         for (int p = 0; p < 4; ++p) {
           const int col = h * kSliceCols + c * 8 + 2 * p;  // first column of the pair in the tile
           const float4 qa = pr[col];
+          if constexpr (MODE != kSums) {
+            // {-Bq pair, Br pair} (kMax2) or {-Bq pair, weights} (kMax): no exponentials
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+              const uint64_t z2 = pk(__uint_as_float(v[8 * r + 2 * p]), __uint_as_float(v[8 * r + 2 * p + 1]));
+              uint64_t u = f2fma(ahA2, z2, f2add(ownA2[r], pk(qa.x, qa.y)));
+              if constexpr (MODE == kMax2) u = f2sub(f2fma(alA2, z2, u), pk(qa.z, qa.w));
+              const float2 uf = upk(u);
+              mxA[r] = fmaxf(mxA[r], fmaxf(uf.x, uf.y));
+            }
+            continue;
+          }
           const float4 qb = pr[col + 1];
           const uint64_t offA2 = pk(qa.x, qa.y), wA2 = pk(qa.z, qa.w);
 #pragma unroll
@@ -340,7 +360,7 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
         if (c + 1 < kChunks) tmem_wait_ld(vv[(c + 1) & 1]);
       }
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
+      for (int r = 0; r < 2 && MODE == kSums; ++r) {
         const float2 a2 = upk(accA[r]), b2 = upk(accB[r]);
         ff_add(hiA[r], loA[r], a2.x + a2.y);
         ff_add(hiB[r], loB[r], b2.x + b2.y);
@@ -363,13 +383,30 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
         double* cb = comb + ((size_t)(h - 1) * kFixed + r * kTile + t) * 3;
+        if constexpr (MODE != kSums) {
+          cb[0] = (double)mxA[r];
+          continue;
+        }
         cb[0] = (double)hiA[r] + (double)loA[r];
         cb[1] = (double)hiB[r] + (double)loB[r];
         cb[2] = (double)hiC[r] + (double)loC[r];
       }
     }
     epi_bar();
-    if (h == 0 && !*(volatile int*)&B->err) {
+    if (MODE != kSums && h == 0 && !*(volatile int*)&B->err) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        float mx = mxA[r];
+        for (int hh = 1; hh < kSlices; ++hh)
+          mx = fmaxf(mx, (float)comb[((size_t)(hh - 1) * kFixed + r * kTile + t) * 3]);
+        if (own[r] < n) {
+          // stream B's maxima are not used under the shared row shift (the B shift is A's)
+          w.rowmax[((int64_t)blockIdx.y * 2 + 0) * n + own[r]] = mx;
+          w.rowmax[((int64_t)blockIdx.y * 2 + 1) * n + own[r]] = mx;
+        }
+      }
+    }
+    if (MODE == kSums && h == 0 && !*(volatile int*)&B->err) {
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
         double sA = (double)hiA[r] + (double)loA[r];
@@ -526,7 +563,8 @@ cudaError_t tc_prepare() {
   const int sm = (int)tc_smem_bytes();
   cudaError_t e = cudaSuccess;
   for (const void* f : {(const void*)tc::k_tc_sweep<true, 0>, (const void*)tc::k_tc_sweep<false, 0>,
-                        (const void*)tc::k_tc_sweep<false, 1>}) {
+                        (const void*)tc::k_tc_sweep<false, 1>, (const void*)tc::k_tc_sweep<true, 0, tc::kMax>,
+                        (const void*)tc::k_tc_sweep<true, 0, tc::kMax2>}) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     // prefer the largest shared-memory carveout: two CTAs per SM need 2 x ~75 KB
     if (e == cudaSuccess)
@@ -573,6 +611,21 @@ cudaError_t tc_launch_sweep(bool rows, int eval, const Geometry& g, const Work& 
     tc::k_tc_sweep<false, 1><<<grid, tc::kThreads, tc_smem_bytes(), st>>>(mf, ms, w, k.n, k.m, tps, k);
   else
     tc::k_tc_sweep<false, 0><<<grid, tc::kThreads, tc_smem_bytes(), st>>>(mf, ms, w, k.n, k.m, tps, k);
+  return cudaGetLastError();
+}
+
+// row maxima on the tensor cores: mode 1 = the prime pass (a z - Bq, no row shift), mode 2 =
+// the refined pass (a z - (Rq + Bq) - Br); per split into w.rowmax, as the row sweep's grid
+cudaError_t tc_launch_rowmax(int mode, const Geometry& g, const Work& w, const Consts& k, int splits, cudaStream_t st) {
+  const int64_t ntiles = (k.m + tc::kStream - 1) / tc::kStream;
+  const int tps = (int)((ntiles + splits - 1) / splits);
+  dim3 grid((unsigned)((k.n + tc::kFixed - 1) / tc::kFixed), (unsigned)splits);
+  const CUtensorMap& mf = *reinterpret_cast<const CUtensorMap*>(g.map_x);
+  const CUtensorMap& ms = *reinterpret_cast<const CUtensorMap*>(g.map_y64);
+  if (mode == 1)
+    tc::k_tc_sweep<true, 0, tc::kMax><<<grid, tc::kThreads, tc_smem_bytes(), st>>>(mf, ms, w, k.n, k.m, tps, k);
+  else
+    tc::k_tc_sweep<true, 0, tc::kMax2><<<grid, tc::kThreads, tc_smem_bytes(), st>>>(mf, ms, w, k.n, k.m, tps, k);
   return cudaGetLastError();
 }
 
