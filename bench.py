@@ -453,8 +453,22 @@ def run_gpu(args, rank, world):
         el = time.perf_counter() - t0
         hst.close()
         e2e_value, _ = job_throughput(n * m * args.e2e_steps, el, dist, devc)
+        # the copies alone: the same pinned host buffers to device tensors, CUDA events
+        srcs = [a for a in (a_h, b_h, r_h, c_h) if a is not None]
+        dsts = [torch.empty(a.shape, dtype=torch.from_numpy(a).dtype, device=devc) for a in srcs]
+        cms = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for dd, a in zip(dsts, srcs):
+                dd.copy_(torch.from_numpy(a), non_blocking=True)
+            e1.record()
+            torch.cuda.synchronize()
+            cms.append(e0.elapsed_time(e1))
         e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d_bytes),
-               "d2h_bytes_per_step": int(8 + 8 * m), "steps": args.e2e_steps}
+               "d2h_bytes_per_step": int(8 + 8 * m), "steps": args.e2e_steps,
+               "ms_per_step": 1e3 * el / args.e2e_steps, "h2d_copy_ms": min(cms)}
 
     info = {}
     if rank == 0 and args.prec == "bf16_tc" and w.kind != "dense" and not args.no_fp32_compare:
