@@ -990,11 +990,29 @@ cudaError_t launch_norms(const Inputs& in, const Consts& k, const Work& w, cudaS
   return cudaGetLastError();
 }
 
+// the K pass's column data in the packed-pair layout: -offA = |y_j|^2 (the float norms that
+// k_norms left in f4[j].x)
+__global__ void k_norm_pairs(const float4* __restrict__ f4, float4* __restrict__ pairs, int64_t m) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < m) store_pair_entry(pairs, j, -f4[j].x, 0.f, 0.f, 0.f);
+}
+
 cudaError_t launch_kmax(const Inputs& in, const Consts& k, const Work& w, const Geometry& g, int prec,
                         cudaStream_t st) {
   if (k.kind == COST_DENSE) {
     k_dense_stats<<<4 * g.sms, kThreads, 0, st>>>(in.C, in.ldc, k.n, k.m, w.scratch);
     return cudaGetLastError();
+  }
+  if (prec == 1 /* LAMP_PREC_BF16_TC */ && g.map_x && w.colq2[1]) {
+    // on the tensor cores, with the products of the bf16 points the iteration uses: the
+    // row data (rowshift[1].x) hold |x_i|^2, the pair data |y_j|^2
+    k_norm_pairs<<<(unsigned)cdiv(k.m, 256), 256, 0, st>>>(w.colq[1], w.colq2[1], k.m);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    Work w2 = w;
+    w2.rowshift[0] = w2.rowshift[1] = w.rowshift[1];
+    w2.colq2[0] = w2.colq2[1] = w.colq2[1];
+    return tc_launch_rowmax(3, g, w2, k, g.rows_split, st);
   }
   // rowmax[split][0][n] = max_j D_ij, rowmax[split][1][n] = max_j -D_ij, D = |x|^2 + |y|^2 - 2 x.y
   return launch_pts<M_KMAX, 0>(in.x, in.y, k.n, k.m, k.d, io_same(w.rowshift[1], nullptr, w.colq[1]), nullptr,

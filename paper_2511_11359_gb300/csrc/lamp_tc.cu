@@ -142,8 +142,10 @@ __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"
 // MODE (row sweeps only): kSums, the iteration's sums; kMax, the row maxima of stream A's
 // exponent without row shift, a z_ij - Bq_j (the prime pass that sets the row shifts);
 // kMax2, the refined row maxima u_ij = a z_ij - (Rq_i + Bq_j) - Br_j with the multiplier's
-// low part (the eta = 0 dual bound's second pass).  The maxima go to rowmax per split.
-constexpr int kSums = 0, kMax = 1, kMax2 = 2;
+// low part (the eta = 0 dual bound's second pass); kKmax, the row maxima of D_ij and of
+// -D_ij, D_ij = |x_i|^2 + |y_j|^2 - 2 x_i.y_j (the K pass: the row data hold |x_i|^2, the
+// pair data -offA = |y_j|^2, columns past m are skipped).  The maxima go to rowmax per split.
+constexpr int kSums = 0, kMax = 1, kMax2 = 2, kKmax = 3;
 template <bool ROWS, int WC, int MODE = kSums>
 __global__ void __launch_bounds__(kThreads, 2)
 k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant__ CUtensorMap map_stream,
@@ -265,7 +267,7 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
     // v^A = a^A z + own + off with a^A rounded to float32 (ah): dropping the low part al
     // changes v by at most half an ulp of a^A z, the order of the rounding of z itself in
     // the MMA's FP32 accumulation (the float32 CUDA-core paths keep al)
-    const uint64_t ahA2 = pk(sp.ahA, sp.ahA);
+    const uint64_t ahA2 = MODE == kKmax ? pk(-2.f, -2.f) : pk(sp.ahA, sp.ahA);
     const uint64_t alA2 = pk(sp.alA, sp.alA);  // kMax2 only
     const float dal = sp.dal;  // stream B: v^B = (a^B - a^A) z + (v^A + dB)
     const uint64_t da2 = pk(dal, dal);
@@ -280,7 +282,8 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
       own[r] = fixed0 + r * kTile + t;
       if (ROWS) {
         const float2 rq = w.rowshift[cur][own[r] < n ? own[r] : n - 1];
-        const float o = MODE == kMax ? 0.f : -rq.x;  // the prime pass has no row shift yet
+        // the prime pass has no row shift yet; the K pass reads |x_i|^2
+        const float o = MODE == kMax ? 0.f : (MODE == kKmax ? rq.x : -rq.x);
         ownA2[r] = pk(o, o);
       } else {
         const int64_t mp = (m + kPad - 1) / kPad * kPad;  // the column data are padded to mp
@@ -293,7 +296,8 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
     }
     float hiA[2] = {0.f, 0.f}, loA[2] = {0.f, 0.f}, hiB[2] = {0.f, 0.f}, loB[2] = {0.f, 0.f};
     float hiC[2] = {0.f, 0.f}, loC[2] = {0.f, 0.f};
-    float mxA[2] = {-INFINITY, -INFINITY};  // kMax, kMax2: running row maxima
+    float mxA[2] = {-INFINITY, -INFINITY};  // kMax, kMax2, kKmax: running row maxima
+    float mnA[2] = {-INFINITY, -INFINITY};  // kKmax: running row maxima of -D
     // packed pair sums of this thread's two points over one streamed tile
     uint64_t accA[2], accB[2], accC[2];
     uint32_t vv[2][16];  // two TMEM chunks: the one evaluated and the one in flight
@@ -330,6 +334,14 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
               uint64_t u = f2fma(ahA2, z2, f2add(ownA2[r], pk(qa.x, qa.y)));
               if constexpr (MODE == kMax2) u = f2sub(f2fma(alA2, z2, u), pk(qa.z, qa.w));
               const float2 uf = upk(u);
+              if constexpr (MODE == kKmax) {
+                const int64_t gcol = (it0 + i) * kStream + col;  // padding columns hold no point
+                const float d0 = gcol < m ? uf.x : -INFINITY, d1 = gcol + 1 < m ? uf.y : -INFINITY;
+                const float e0 = gcol < m ? -uf.x : -INFINITY, e1 = gcol + 1 < m ? -uf.y : -INFINITY;
+                mxA[r] = fmaxf(mxA[r], fmaxf(d0, d1));
+                mnA[r] = fmaxf(mnA[r], fmaxf(e0, e1));
+                continue;
+              }
               mxA[r] = fmaxf(mxA[r], fmaxf(uf.x, uf.y));
             }
             continue;
@@ -385,6 +397,7 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
         double* cb = comb + ((size_t)(h - 1) * kFixed + r * kTile + t) * 3;
         if constexpr (MODE != kSums) {
           cb[0] = (double)mxA[r];
+          cb[1] = (double)mnA[r];
           continue;
         }
         cb[0] = (double)hiA[r] + (double)loA[r];
@@ -396,13 +409,16 @@ k_tc_sweep(const __grid_constant__ CUtensorMap map_fixed, const __grid_constant_
     if (MODE != kSums && h == 0 && !*(volatile int*)&B->err) {
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
-        float mx = mxA[r];
-        for (int hh = 1; hh < kSlices; ++hh)
+        float mx = mxA[r], mn = mnA[r];
+        for (int hh = 1; hh < kSlices; ++hh) {
           mx = fmaxf(mx, (float)comb[((size_t)(hh - 1) * kFixed + r * kTile + t) * 3]);
+          mn = fmaxf(mn, (float)comb[((size_t)(hh - 1) * kFixed + r * kTile + t) * 3 + 1]);
+        }
         if (own[r] < n) {
-          // stream B's maxima are not used under the shared row shift (the B shift is A's)
+          // the K pass: max D and max -D; otherwise stream B's maxima are not used under the
+          // shared row shift (the B shift is A's)
           w.rowmax[((int64_t)blockIdx.y * 2 + 0) * n + own[r]] = mx;
-          w.rowmax[((int64_t)blockIdx.y * 2 + 1) * n + own[r]] = mx;
+          w.rowmax[((int64_t)blockIdx.y * 2 + 1) * n + own[r]] = MODE == kKmax ? mn : mx;
         }
       }
     }
@@ -564,7 +580,8 @@ cudaError_t tc_prepare() {
   cudaError_t e = cudaSuccess;
   for (const void* f : {(const void*)tc::k_tc_sweep<true, 0>, (const void*)tc::k_tc_sweep<false, 0>,
                         (const void*)tc::k_tc_sweep<false, 1>, (const void*)tc::k_tc_sweep<true, 0, tc::kMax>,
-                        (const void*)tc::k_tc_sweep<true, 0, tc::kMax2>}) {
+                        (const void*)tc::k_tc_sweep<true, 0, tc::kMax2>,
+                        (const void*)tc::k_tc_sweep<true, 0, tc::kKmax>}) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     // prefer the largest shared-memory carveout: two CTAs per SM need 2 x ~75 KB
     if (e == cudaSuccess)
@@ -615,7 +632,8 @@ cudaError_t tc_launch_sweep(bool rows, int eval, const Geometry& g, const Work& 
 }
 
 // row maxima on the tensor cores: mode 1 = the prime pass (a z - Bq, no row shift), mode 2 =
-// the refined pass (a z - (Rq + Bq) - Br); per split into w.rowmax, as the row sweep's grid
+// the refined pass (a z - (Rq + Bq) - Br), mode 3 = the K pass (max D and max -D); per split
+// into w.rowmax, as the row sweep's grid
 cudaError_t tc_launch_rowmax(int mode, const Geometry& g, const Work& w, const Consts& k, int splits, cudaStream_t st) {
   const int64_t ntiles = (k.m + tc::kStream - 1) / tc::kStream;
   const int tps = (int)((ntiles + splits - 1) / splits);
@@ -624,8 +642,10 @@ cudaError_t tc_launch_rowmax(int mode, const Geometry& g, const Work& w, const C
   const CUtensorMap& ms = *reinterpret_cast<const CUtensorMap*>(g.map_y64);
   if (mode == 1)
     tc::k_tc_sweep<true, 0, tc::kMax><<<grid, tc::kThreads, tc_smem_bytes(), st>>>(mf, ms, w, k.n, k.m, tps, k);
-  else
+  else if (mode == 2)
     tc::k_tc_sweep<true, 0, tc::kMax2><<<grid, tc::kThreads, tc_smem_bytes(), st>>>(mf, ms, w, k.n, k.m, tps, k);
+  else
+    tc::k_tc_sweep<true, 0, tc::kKmax><<<grid, tc::kThreads, tc_smem_bytes(), st>>>(mf, ms, w, k.n, k.m, tps, k);
   return cudaGetLastError();
 }
 
