@@ -59,8 +59,8 @@ NCU_TRAFFIC = {
     ("highdim", "bf16_tc", 32768, 64): {
         "sources": ["paper_2511_11359_gb300/csrc/lamp_tc.cu", "paper_2511_11359_gb300/csrc/lamp_tc.cuh",
                     "paper_2511_11359_gb300/csrc/lamp_async.cuh", "paper_2511_11359_gb300/csrc/lamp_common.cuh"],
-        "sha256": "13bcd0b5775d9555d71f7c028c41f4d586d9a929fe623278c7f7aa2ad14442e9",
-        "row_sweep": 9239808, "col_sweep": 9990656},
+        "sha256": "7c3a6dc1c18d6bdc294b81a37c05316fd98c0753effa207139a19e8aa6b02602",
+        "row_sweep": 9230336, "col_sweep": 9992448},
     ("image_grid", "fp32", 4096, 0): {
         "sources": ["paper_2511_11359_gb300/csrc/lamp_dense.cu", "paper_2511_11359_gb300/csrc/lamp_async.cuh",
                     "paper_2511_11359_gb300/csrc/lamp_common.cuh"],
