@@ -60,7 +60,7 @@ NCU_TRAFFIC = {
         "sources": ["paper_2511_11359_gb300/csrc/lamp_tc.cu", "paper_2511_11359_gb300/csrc/lamp_tc.cuh",
                     "paper_2511_11359_gb300/csrc/lamp_async.cuh", "paper_2511_11359_gb300/csrc/lamp_common.cuh"],
         "sha256": "7c3a6dc1c18d6bdc294b81a37c05316fd98c0753effa207139a19e8aa6b02602",
-        "row_sweep": 9230336, "col_sweep": 9992448},
+        "row_sweep": 9203712, "col_sweep": 9990144},
     ("image_grid", "fp32", 4096, 0): {
         "sources": ["paper_2511_11359_gb300/csrc/lamp_dense.cu", "paper_2511_11359_gb300/csrc/lamp_async.cuh",
                     "paper_2511_11359_gb300/csrc/lamp_common.cuh"],
