@@ -155,3 +155,20 @@ def test_tc_run_is_deterministic_across_graph_lengths(n, iters):
         s.close()
     for key in ("nu", "theta", "row_shifts"):
         assert np.array_equal(out[0][key], out[1][key]), key
+
+
+@pytest.mark.parametrize("n,m,d", [(300, 257, 17), (1000, 999, 64), (4096, 3000, 64)])
+def test_tc_k_pass_matches_the_rounded_cost(n, m, d):
+    """A tensor-core context takes K = max C from its own sweep (D = |x|^2 + |y|^2 - 2 x.y over
+    the MMA's products of the bf16 points, columns past m skipped): K matches the maximum
+    of the oracle's cost on the rounded points to float32 rounding."""
+    import torch
+    import paper_2511_11359_gb300 as L
+
+    w = W.highdim(n=n, m=m, d=d, seed=n + m)
+    dev = torch.device("cuda", 0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    with L.Lamp(t(w.r), t(w.c), x=t(w.x), y=t(w.y), prec="bf16_tc") as s:
+        K = s.objective()["K"]
+    Kref = float(O.sqeuclid_cost(W.bf16_round(w.x), W.bf16_round(w.y)).max())
+    assert abs(K - Kref) <= 1e-6 * Kref, (K, Kref)
